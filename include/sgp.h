@@ -1,0 +1,175 @@
+/*
+ * sgp.h -- C ABI of the GB300 propagator for the rotating spin-orbit-coupled
+ * spin-2 Gross-Pitaevskii system, integrated with the compact splitting
+ * Fourier spectral method of arXiv 2603.25282.
+ *
+ * Model (Sec. 1, Eq. (CGPEs)):
+ *   i d/dt Psi = (H0 I + c1 F.f - gamma S) Psi + c2 A00 A conj(Psi),
+ *   H0 = -Lap/2 + V + c0 rho - Omega L_z,  V = (gx^2 x^2 + gy^2 y^2 [+ gz^2 z^2])/2.
+ * Method (Sec. 3): in the rotating frame of Eq. (mapping) the linear flow
+ * (Laplace + SOC + Omega f_z, Eq. (linearEQ2)) is exact per Fourier mode
+ * (Eq. (sl1)); the nonlinear flow is exact per grid point (Eq. (solution2))
+ * with the trap taken at R(t)x; they are composed as TS2 (Algorithm 1) or TS4
+ * (Sec. 3.3).
+ *
+ * Conventions shared by every entry point:
+ *   - Field layout: complex interleaved (re, im), shape
+ *     [batch][5][nz][ny][nx] with x fastest; component order l = 2,1,0,-1,-2
+ *     (Sec. 1, the vector Psi).  2D grids have nz = 1.
+ *   - Element type: complex64 (two floats) for SGP_F32 contexts, complex128
+ *     (two doubles) for SGP_F64 contexts.  SGP_F32 contexts still keep the
+ *     time t, the rotation angle Omega t, the linear-flow phase angles and all
+ *     observable sums in FP64.
+ *   - Grid: x_j = -L + j h, h = 2L/N, N even (Sec. 3.1); supported N per
+ *     axis: 2^a 3^b with 16 <= N <= 1024 (b <= 1).
+ *   - Frame: the context stores the rotating-frame field
+ *     phi_l(x,t) = exp(-i l Omega t) psi_l(R(t) x, t) of Eq. (mapping); at
+ *     t = 0 it equals the lab-frame field.
+ *   - Ownership: every pointer argument stays owned by the caller; the
+ *     context owns its device buffers and frees them in sgp_destroy.
+ *   - Streams: all device work of a context is issued on the CUDA stream
+ *     given at creation (a cudaStream_t passed as void*; NULL = the legacy
+ *     default stream).  Calls documented as asynchronous return before the
+ *     GPU work completes.
+ *   - Errors: every call returns an sgp_status; on failure the context keeps
+ *     a message readable with sgp_last_error.  No call throws or aborts.
+ *     A context is not thread-safe: one host thread at a time.
+ */
+#ifndef SGP_H
+#define SGP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgp_ctx sgp_ctx;
+
+typedef enum {
+  SGP_OK = 0,
+  SGP_EINVAL = 1,        /* bad argument (size, pointer, parameter, dt)   */
+  SGP_ENOMEM = 2,        /* device or host allocation failed              */
+  SGP_ECUDA = 3,         /* a CUDA runtime call failed (see last_error)   */
+  SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up            */
+  SGP_ENONFINITE = 5,    /* a NaN/Inf was detected in the observables     */
+  SGP_ESTATE = 6,        /* call out of order (e.g. step before set_state)*/
+  SGP_EUNSUPPORTED = 7   /* valid request this build does not implement   */
+} sgp_status;
+
+typedef enum { SGP_F32 = 32, SGP_F64 = 64 } sgp_prec;
+
+/* Compositions of Sec. 3.3.  TS2: N(tau/2) L(tau) N(tau/2) (Algorithm 1).
+ * TS4: N(a1 tau) L(b1 tau) N(a2 tau) L(b2 tau) N(a2 tau) L(b1 tau) N(a1 tau)
+ * with the fourth-order coefficients of Sec. 3.3, the nonlinear flow taking
+ * the a_j and the linear flow the b_j.  Time advances in the L substeps. */
+typedef enum { SGP_TS2 = 0, SGP_TS4 = 1 } sgp_scheme;
+
+/* Substep kinds for sgp_substep. */
+typedef enum { SGP_SUB_NONLINEAR = 0, SGP_SUB_LINEAR = 1 } sgp_substep_kind;
+
+/* Parameters of Eq. (CGPEs) and the harmonic trap (harmonic). */
+typedef struct {
+  double omega;   /* angular velocity Omega                       */
+  double gamma;   /* spin-orbit coupling strength gamma           */
+  double c0, c1, c2;  /* mean-field, spin-exchange, singlet-pairing */
+  double gx, gy, gz;  /* trap frequencies gamma_x, gamma_y, gamma_z */
+} sgp_params;
+
+/* Observables of Sec. 2 for one batch member, lab-frame quantities computed
+ * from the rotating-frame field (mass, <L_z>, |grad|^2, the rho/F/A00 terms
+ * and the SOC term are frame invariant; the trap and widths use R(t)x).
+ * Integrals are h^d-weighted grid sums; derivatives are spectral. */
+typedef struct {
+  double t;             /* current time                                   */
+  double mass;          /* N(t) = sum_l ||psi_l||^2                        */
+  double energy;        /* E(t), Sec. 2 "Mass and energy"                  */
+  double magnetization; /* M(t) = sum_l l ||psi_l||^2                      */
+  double lz;            /* <L_z>(t)                                        */
+  double comp_mass[5];  /* ||psi_l||^2, l = 2..-2                          */
+  double width2[3];     /* delta_x, delta_y, delta_z of Eq. (ConWid)       */
+  double e_kin;         /* sum (1/2)|grad psi|^2                           */
+  double e_pot;         /* sum V rho                                       */
+  double e_rot;         /* -Omega <L_z>                                    */
+  double e_int;         /* c0/2 rho^2 + c1/2 (|F+|^2+Fz^2) + c2/2 |A00|^2  */
+  double e_soc;         /* -gamma Psi^H S Psi                              */
+} sgp_obs;
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int sgp_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* sgp_status_string(sgp_status s);
+
+/* Create a context for `batch` independent fields on a dim-D grid
+ * (Sec. 3.1 grids).  n[0..dim-1] and L[0..dim-1] are given in (x, y, z)
+ * order; L is the half-width of [-L, L].  prec is SGP_F32 or SGP_F64.
+ * device is the CUDA ordinal; stream a cudaStream_t (or NULL).
+ * Allocates the field, the FFT twiddle tables and the observable scratch on
+ * `device`.  Errors: SGP_EINVAL for dim not in {2,3}, unsupported N, L <= 0,
+ * batch < 1 or a NULL out; SGP_ENOMEM/SGP_ECUDA on allocation failure (no
+ * context is returned then).  Parameters default to all zero with unit trap
+ * frequencies; the field to zero at t = 0. */
+sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch,
+                           int prec, int device, void* stream, sgp_ctx** out);
+
+/* Set the physical parameters (Sec. 1).  All batch members share them.
+ * Synchronous on the host; takes effect for work issued afterwards.
+ * Errors: SGP_EINVAL for NULL or non-finite values. */
+sgp_status sgp_set_params(sgp_ctx* ctx, const sgp_params* p);
+
+/* Copy a field into the context and set the time to t0.  `src` holds
+ * batch*5*nz*ny*nx complex elements of the context precision in the layout
+ * above; src_on_device != 0 means a device pointer on the context device.
+ * At t0 the rotating frame coincides with the lab frame only if t0 = 0;
+ * otherwise `src` is taken as the rotating-frame field at t0.  The copy is
+ * ordered on the context stream; a host `src` may be reused on return.
+ * Errors: SGP_EINVAL for NULL or non-finite t0. */
+sgp_status sgp_set_state(sgp_ctx* ctx, const void* src, int src_on_device,
+                         double t0);
+
+/* Copy the current (rotating-frame) field out, same layout as set_state.
+ * With dst_on_device == 0 the call synchronises the context stream before
+ * returning; with a device pointer it is asynchronous. */
+sgp_status sgp_get_state(sgp_ctx* ctx, void* dst, int dst_on_device);
+
+/* Current time t (host copy, FP64). */
+sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
+
+/* Advance every batch member by nsteps steps of size dt with the given
+ * composition (Sec. 3.3; TS2 is Algorithm 1).  Adjacent nonlinear substeps of
+ * consecutive steps, taken at the same time, are merged into one exact
+ * nonlinear flow (the flow property of Eq. (solution2)), so a call costs
+ * nsteps linear and nsteps+1 nonlinear substeps for TS2.  The field is in
+ * physical space on return.  Asynchronous on the context stream.
+ * Errors: SGP_EINVAL for nsteps < 0, dt <= 0 or non-finite dt; SGP_ESTATE
+ * before sgp_set_state; SGP_ECUDA if a launch fails. */
+sgp_status sgp_step(sgp_ctx* ctx, long long nsteps, double dt, int scheme);
+
+/* Apply one substep of size delta (delta may be negative, Sec. 3.3 TS4):
+ * SGP_SUB_NONLINEAR applies the exact flow (solution2) at the current time;
+ * SGP_SUB_LINEAR applies the exact flow (sl1) and advances the time by delta.
+ * Asynchronous. */
+sgp_status sgp_substep(sgp_ctx* ctx, int kind, double delta);
+
+/* Observables of Sec. 2 for every batch member into out[0..batch-1].
+ * Synchronises the context stream.  Returns SGP_ENONFINITE (with out
+ * filled) if any sum is NaN or Inf. */
+sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
+
+/* Wait for all work issued on the context stream. */
+sgp_status sgp_synchronize(sgp_ctx* ctx);
+
+/* Number of kernels this context has launched so far (for accounting). */
+long long sgp_launch_count(const sgp_ctx* ctx);
+
+/* Free the context and its device memory (synchronises first).  NULL is a
+ * no-op. */
+sgp_status sgp_destroy(sgp_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none); static storage for
+ * a NULL ctx (creation errors).  Valid until the next call on ctx. */
+const char* sgp_last_error(const sgp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGP_H */

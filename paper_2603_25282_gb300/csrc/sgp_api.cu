@@ -1,0 +1,672 @@
+// sgp_api.cu -- the C ABI declared in include/sgp.h: context management,
+// per-substep tables, pass orchestration of TS2/TS4 and the observables.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sgp.h"
+#include "sgp_launch.cuh"
+
+using namespace sgp;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// TS4 coefficients of Sec. 3.3 (c = 2^(1/3)).
+const double kCbrt2 = std::cbrt(2.0);
+const double kA1 = 1.0 / (2.0 * (2.0 - kCbrt2));
+const double kA2 = (1.0 - kCbrt2) / (2.0 * (2.0 - kCbrt2));
+const double kB1 = 1.0 / (2.0 - kCbrt2);
+const double kB2 = -kCbrt2 / (2.0 - kCbrt2);
+
+// ----------------------------------------------------------------------------
+// table kernels (FP64 arithmetic, stored in the context precision)
+// ----------------------------------------------------------------------------
+// W_N^k = exp(-2 pi i k / N), k < N.
+template <typename R>
+__global__ void k_twiddles(int N, cplx<R>* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)N, &s, &c);
+  out[k] = mkc((R)c, (R)s);
+}
+
+// Per-substep tables of the linear flow over delta (Sec. 3.1, Eq. (sl1)):
+//  lam[(|p|, |q|)] = (ahat, cp, sp) of U = exp(i delta lambda n.sigma/2),
+//    lambda = sqrt(Omega^2 + gamma^2 |nu_perp|^2),
+//    U11 = cos(th/2) - i sin(th/2) Omega/lambda = cp * ahat,
+//    U12 = sin(th/2) gamma (nu_x - i nu_y)/lambda = sp * (nu_x - i nu_y)/|nu_perp|;
+//  kin_a[p] = exp(-i nu_p^2 delta/2) / N_a for each axis a (the 1/N of the
+//    forward transforms is folded in here).
+template <typename R>
+__global__ void k_linear_tables(double delta, double omega, double gamma, int NX, int NY,
+                                int NZ, double Lx, double Ly, double Lz, R* lam,
+                                cplx<R>* kx, cplx<R>* ky, cplx<R>* kz) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int hq = NY / 2 + 1;
+  const int nlam = (NX / 2 + 1) * hq;
+  if (id < nlam) {
+    const int ap = id / hq, aq = id - ap * hq;
+    const double nup = kPi * ap / Lx, nuq = kPi * aq / Ly;
+    const double nperp = sqrt(nup * nup + nuq * nuq);
+    const double lamb = sqrt(omega * omega + gamma * gamma * nperp * nperp);
+    double ar = 1.0, ai = 0.0, cp = 1.0, sp = 0.0;
+    if (lamb > 0.0) {
+      double s, c;
+      sincos(0.5 * delta * lamb, &s, &c);
+      const double ur = c, ui = -s * omega / lamb;
+      cp = sqrt(ur * ur + ui * ui);
+      if (cp > 0.0) {
+        ar = ur / cp;
+        ai = ui / cp;
+      }
+      sp = s * gamma * nperp / lamb;
+    }
+    lam[4 * id + 0] = (R)ar;
+    lam[4 * id + 1] = (R)ai;
+    lam[4 * id + 2] = (R)cp;
+    lam[4 * id + 3] = (R)sp;
+  }
+  auto kin = [&](int k, int N, double L, cplx<R>* out) {
+    const int ks = k < N / 2 ? k : k - N;
+    const double nu = kPi * ks / L;
+    double s, c;
+    sincos(-0.5 * nu * nu * delta, &s, &c);
+    out[k] = mkc((R)(c / N), (R)(s / N));
+  };
+  if (id < NX) kin(id, NX, Lx, kx);
+  if (id < NY) kin(id, NY, Ly, ky);
+  if (id < NZ) kin(id, NZ, Lz, kz);
+}
+
+__global__ void k_set_time(double* t, double v) { *t = v; }
+
+// ----------------------------------------------------------------------------
+// context
+// ----------------------------------------------------------------------------
+struct LinTables {
+  double delta = 0.0;
+  void* lam = nullptr;
+  void* kin[3] = {nullptr, nullptr, nullptr};
+};
+
+}  // namespace
+
+struct sgp_ctx {
+  int dim = 2;
+  int n[3] = {1, 1, 1};
+  double L[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  int batch = 1;
+  int prec = SGP_F32;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  long long ntot = 0;
+  size_t elem = 8;
+  void* field = nullptr;
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  double* t_dev = nullptr;
+  double t = 0.0;
+  sgp_params prm{};
+  bool have_params = false;
+  bool have_state = false;
+  std::vector<LinTables> tables;    // cache keyed by delta (params fixed)
+  double* partials = nullptr;       // observables scratch
+  size_t partials_len = 0;
+  double* obs_dev = nullptr;        // [batch][OB_NT]
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_err;
+
+sgp_status fail(sgp_ctx* c, sgp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_err = buf;
+  return s;
+}
+
+#define SGP_CUDA(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((ctx), SGP_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool finite_params(const sgp_params* p) {
+  const double v[8] = {p->omega, p->gamma, p->c0, p->c1, p->c2, p->gx, p->gy, p->gz};
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+void free_tables(sgp_ctx* c) {
+  for (auto& t : c->tables) {
+    cudaFree(t.lam);
+    for (void* k : t.kin) cudaFree(k);
+  }
+  c->tables.clear();
+}
+
+template <typename R>
+sgp_status get_tables(sgp_ctx* c, double delta, const LinTables** out) {
+  for (auto& t : c->tables)
+    if (t.delta == delta) {
+      *out = &t;
+      return SGP_OK;
+    }
+  if (c->tables.size() >= 8) free_tables(c);
+  LinTables t;
+  t.delta = delta;
+  const int NX = c->n[0], NY = c->n[1], NZ = c->n[2];
+  const size_t nlam = (size_t)(NX / 2 + 1) * (NY / 2 + 1);
+  SGP_CUDA(c, cudaMalloc(&t.lam, nlam * 4 * sizeof(R)));
+  for (int a = 0; a < 3; ++a) SGP_CUDA(c, cudaMalloc(&t.kin[a], (size_t)c->n[a] * sizeof(cplx<R>)));
+  const int work = (int)std::max<size_t>(nlam, (size_t)std::max(NX, std::max(NY, NZ)));
+  k_linear_tables<R><<<(work + 255) / 256, 256, 0, c->stream>>>(
+      delta, c->prm.omega, c->prm.gamma, NX, NY, NZ, c->L[0], c->L[1], c->L[2], (R*)t.lam,
+      (cplx<R>*)t.kin[0], (cplx<R>*)t.kin[1], (cplx<R>*)t.kin[2]);
+  c->launches++;
+  SGP_CUDA(c, cudaGetLastError());
+  c->tables.push_back(t);
+  *out = &c->tables.back();
+  return SGP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// passes
+// ----------------------------------------------------------------------------
+template <typename R>
+sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
+  XPassArgs<R> a{};
+  a.field = (cplx<R>*)c->field;
+  a.tw = (const cplx<R>*)c->tw[0];
+  a.ntot = c->ntot;
+  a.rows = c->n[1] * c->n[2];
+  a.ny = c->n[1];
+  a.mode = mode;
+  a.x0 = (R)-c->L[0];
+  a.hx = (R)c->h[0];
+  a.y0 = (R)-c->L[1];
+  a.hy = (R)c->h[1];
+  a.z0 = c->dim == 3 ? (R)-c->L[2] : (R)0;
+  a.hz = c->dim == 3 ? (R)c->h[2] : (R)0;
+  a.delta = (R)delta;
+  a.c0p = (R)(c->prm.c0 + c->prm.c2 / 5.0);
+  a.c1 = (R)c->prm.c1;
+  a.c2 = (R)c->prm.c2;
+  a.gx2h = (R)(0.5 * c->prm.gx * c->prm.gx);
+  a.gy2h = (R)(0.5 * c->prm.gy * c->prm.gy);
+  a.gz2h = c->dim == 3 ? (R)(0.5 * c->prm.gz * c->prm.gz) : (R)0;
+  a.omega = c->prm.omega;
+  a.t_base = c->t_dev;
+  a.t_off = t_off;
+  c->launches++;
+  SGP_CUDA(c, launch_xpass<R>(c->n[0], a, c->batch, c->stream));
+  return SGP_OK;
+}
+
+// axis 1: lines along y (planes = z slices); axis 2: lines along z (planes = y rows)
+template <typename R>
+sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
+  LPassArgs<R> a{};
+  a.field = (cplx<R>*)c->field;
+  a.tw = (const cplx<R>*)c->tw[axis];
+  a.ntot = c->ntot;
+  a.nx = c->n[0];
+  const long long nxy = (long long)c->n[0] * c->n[1];
+  int planes;
+  if (axis == 1) {
+    a.line_stride = c->n[0];
+    a.plane_stride = nxy;
+    planes = c->n[2];
+  } else {
+    a.line_stride = nxy;
+    a.plane_stride = c->n[0];
+    planes = c->n[1];
+  }
+  a.mode = mode;
+  a.axis = axis;
+  a.NX = c->n[0];
+  a.NY = c->n[1];
+  if (t) {
+    a.lam = (const R*)t->lam;
+    a.kx = (const cplx<R>*)t->kin[0];
+    a.ky = (const cplx<R>*)t->kin[1];
+    a.kz = (const cplx<R>*)t->kin[2];
+  }
+  a.pix = (R)(kPi / c->L[0]);
+  a.piy = (R)(kPi / c->L[1]);
+  c->launches++;
+  SGP_CUDA(c, launch_linepass<R>(c->n[axis], a, planes, c->batch, c->stream));
+  return SGP_OK;
+}
+
+#define SGP_TRY(x)                   \
+  do {                               \
+    sgp_status s_ = (x);             \
+    if (s_ != SGP_OK) return s_;     \
+  } while (0)
+
+// Linear flow over delta between x-passes.  Entry: x-spectral (the x-pass
+// has done its forward transform).  Exit: x-spectral.
+template <typename R>
+sgp_status linear_middle(sgp_ctx* c, double delta) {
+  const LinTables* t = nullptr;
+  SGP_TRY(get_tables<R>(c, delta, &t));
+  if (c->dim == 2) {
+    SGP_TRY(line_pass<R>(c, 1, LP_FWD | LP_MIX | LP_INV, t));
+  } else {
+    SGP_TRY(line_pass<R>(c, 1, LP_FWD, nullptr));
+    SGP_TRY(line_pass<R>(c, 2, LP_FWD | LP_MIX | LP_INV, t));
+    SGP_TRY(line_pass<R>(c, 1, LP_INV, nullptr));
+  }
+  return SGP_OK;
+}
+
+// Run nsteps of the composition.  Adjacent nonlinear substeps at the same
+// time are merged (exact flow property), so the pass sequence is
+//   N  L  N  L ... L  N   (N as x-passes, L as the line passes).
+template <typename R>
+sgp_status run_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
+  // substep pattern of one step, Sec. 3.3
+  std::vector<std::pair<char, double>> seq;
+  if (scheme == SGP_TS2) {
+    seq = {{'N', 0.5}, {'L', 1.0}, {'N', 0.5}};
+  } else {
+    seq = {{'N', kA1}, {'L', kB1}, {'N', kA2}, {'L', kB2},
+           {'N', kA2}, {'L', kB1}, {'N', kA1}};
+  }
+  const double t0 = c->t;
+  c->launches++;
+  k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, t0);
+  SGP_CUDA(c, cudaGetLastError());
+  // first nonlinear substep (physical in, x-spectral out)
+  SGP_TRY(x_pass<R>(c, XP_NL | XP_FWD, seq[0].second * dt, 0.0));
+  const int inner = (int)seq.size();
+  for (long long s = 0; s < nsteps; ++s) {
+    double toff = (double)s * dt;      // offset of this step's start from t0
+    double sub = 0.0;                  // time advanced within the step
+    for (int k = 1; k < inner; ++k) {
+      if (seq[k].first == 'L') {
+        const double d = seq[k].second * dt;
+        SGP_TRY(linear_middle<R>(c, d));
+        sub += seq[k].second;
+      } else {
+        double coef = seq[k].second;
+        const bool last_in_step = (k == inner - 1);
+        const bool last = last_in_step && (s == nsteps - 1);
+        if (last_in_step && !last) coef += seq[0].second;   // merge with next step's first N
+        const double tn = last_in_step ? (double)(s + 1) * dt : toff + sub * dt;
+        const int mode = last ? (XP_INV | XP_NL) : (XP_INV | XP_NL | XP_FWD);
+        SGP_TRY(x_pass<R>(c, mode, coef * dt, tn));
+      }
+    }
+  }
+  c->t = t0 + (double)nsteps * dt;
+  return SGP_OK;
+}
+
+template <typename R>
+sgp_status substep(sgp_ctx* c, int kind, double delta) {
+  c->launches++;
+  k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, c->t);
+  SGP_CUDA(c, cudaGetLastError());
+  if (kind == SGP_SUB_NONLINEAR) {
+    SGP_TRY(x_pass<R>(c, XP_NL, delta, 0.0));
+  } else {
+    SGP_TRY(x_pass<R>(c, XP_FWD, 0.0, 0.0));
+    SGP_TRY(linear_middle<R>(c, delta));
+    SGP_TRY(x_pass<R>(c, XP_INV, 0.0, 0.0));
+    c->t += delta;
+  }
+  return SGP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// observables
+// ----------------------------------------------------------------------------
+template <typename R>
+sgp_status observables(sgp_ctx* c, sgp_obs* out) {
+  const int NX = c->n[0];
+  const PassGeom gx = xpass_geom<R>(NX);
+  const int rows = c->n[1] * c->n[2];
+  const int nbx = (rows + gx.rows_or_tile - 1) / gx.rows_or_tile;
+  ObsXArgs<R> ax{};
+  ax.ntot = c->ntot;
+  ax.rows = rows;
+  ax.ny = c->n[1];
+  ax.x0 = -c->L[0];
+  ax.hx = c->h[0];
+  ax.y0 = -c->L[1];
+  ax.hy = c->h[1];
+  ax.z0 = c->dim == 3 ? -c->L[2] : 0.0;
+  ax.hz = c->dim == 3 ? c->h[2] : 0.0;
+  ax.omega = c->prm.omega;
+  ax.t = c->t;
+  ax.c0 = c->prm.c0;
+  ax.c1 = c->prm.c1;
+  ax.c2 = c->prm.c2;
+  ax.gx2h = 0.5 * c->prm.gx * c->prm.gx;
+  ax.gy2h = 0.5 * c->prm.gy * c->prm.gy;
+  ax.gz2h = c->dim == 3 ? 0.5 * c->prm.gz * c->prm.gz : 0.0;
+  ax.partials = c->partials;
+  ax.nblocks = nbx;
+  ax.field = (const cplx<R>*)c->field;
+  ax.tw = (const cplx<R>*)c->tw[0];
+  ax.dnu = (R)(kPi / c->L[0] / NX);
+  ax.NX = NX;
+  c->launches++;
+  SGP_CUDA(c, launch_obs_x<R>(NX, ax, c->batch, c->stream));
+  c->launches++;
+  k_reduce_partials<<<(c->batch * OBX_NT + 127) / 128, 128, 0, c->stream>>>(
+      c->partials, nbx, OBX_NT, c->batch, c->obs_dev, OB_NT, 0);
+  SGP_CUDA(c, cudaGetLastError());
+  for (int axis = 1; axis < c->dim; ++axis) {
+    const int NL = c->n[axis];
+    const PassGeom gl = linepass_geom<R>(NL);
+    ObsLArgs<R> al{};
+    static_cast<ObsArgsBase&>(al) = static_cast<const ObsArgsBase&>(ax);
+    al.field = (const cplx<R>*)c->field;
+    al.tw = (const cplx<R>*)c->tw[axis];
+    al.nx = NX;
+    const long long nxy = (long long)c->n[0] * c->n[1];
+    int planes;
+    if (axis == 1) {
+      al.line_stride = NX;
+      al.plane_stride = nxy;
+      planes = c->n[2];
+    } else {
+      al.line_stride = nxy;
+      al.plane_stride = NX;
+      planes = c->n[1];
+    }
+    al.axis = axis;
+    al.dnu = (R)(kPi / c->L[axis] / NL);
+    al.NL = NL;
+    const int tiles = (NX + gl.rows_or_tile - 1) / gl.rows_or_tile;
+    al.nblocks = tiles * planes;
+    c->launches++;
+    SGP_CUDA(c, launch_obs_line<R>(NL, al, planes, c->batch, c->stream));
+    c->launches++;
+    k_reduce_partials<<<(c->batch * OBL_NT + 127) / 128, 128, 0, c->stream>>>(
+        c->partials, al.nblocks, OBL_NT, c->batch, c->obs_dev, OB_NT,
+        axis == 1 ? OB_KY : OB_KZ);
+    SGP_CUDA(c, cudaGetLastError());
+  }
+  std::vector<double> h((size_t)c->batch * OB_NT, 0.0);
+  SGP_CUDA(c, cudaMemcpyAsync(h.data(), c->obs_dev, h.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double cell = c->h[0] * c->h[1] * (c->dim == 3 ? c->h[2] : 1.0);
+  bool finite = true;
+  for (int m = 0; m < c->batch; ++m) {
+    const double* s = &h[(size_t)m * OB_NT];
+    if (c->dim == 2) {
+      // OB_KZ slot is not written in 2D (the z-line pass does not run)
+    }
+    sgp_obs o{};
+    o.t = c->t;
+    o.mass = 0.0;
+    o.magnetization = 0.0;
+    for (int k = 0; k < 5; ++k) {
+      o.comp_mass[k] = cell * s[OB_M0 + k];
+      o.mass += o.comp_mass[k];
+      o.magnetization += (2 - k) * o.comp_mass[k];
+    }
+    o.width2[0] = cell * s[OB_WX];
+    o.width2[1] = cell * s[OB_WY];
+    o.width2[2] = cell * s[OB_WZ];
+    const double kz = c->dim == 3 ? s[OB_KZ] : 0.0;
+    o.e_kin = cell * (s[OB_KX] + s[OB_KY] + kz);
+    o.e_pot = cell * s[OB_POT];
+    o.lz = cell * (s[OB_LZX] + s[OB_LZY]);
+    o.e_rot = -c->prm.omega * o.lz;
+    o.e_int = cell * s[OB_INT];
+    o.e_soc = -c->prm.gamma * cell * (s[OB_SOCX] + s[OB_SOCY]);
+    o.energy = o.e_kin + o.e_pot + o.e_rot + o.e_int + o.e_soc;
+    const double chk[6] = {o.mass, o.energy, o.magnetization, o.lz, o.width2[0], o.width2[1]};
+    for (double v : chk)
+      if (!std::isfinite(v)) finite = false;
+    out[m] = o;
+  }
+  if (!finite) return fail(c, SGP_ENONFINITE, "non-finite observable");
+  return SGP_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int sgp_version(void) { return 100; }
+
+const char* sgp_status_string(sgp_status s) {
+  switch (s) {
+    case SGP_OK: return "SGP_OK";
+    case SGP_EINVAL: return "SGP_EINVAL";
+    case SGP_ENOMEM: return "SGP_ENOMEM";
+    case SGP_ECUDA: return "SGP_ECUDA";
+    case SGP_ETIMEOUT: return "SGP_ETIMEOUT";
+    case SGP_ENONFINITE: return "SGP_ENONFINITE";
+    case SGP_ESTATE: return "SGP_ESTATE";
+    case SGP_EUNSUPPORTED: return "SGP_EUNSUPPORTED";
+  }
+  return "unknown";
+}
+
+const char* sgp_last_error(const sgp_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, int prec,
+                           int device, void* stream, sgp_ctx** out) {
+  g_create_err.clear();
+  if (!out || !n || !L) return fail(nullptr, SGP_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(nullptr, SGP_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+  if (prec != SGP_F32 && prec != SGP_F64)
+    return fail(nullptr, SGP_EINVAL, "prec must be SGP_F32 or SGP_F64");
+  if (batch < 1 || batch > 65535)
+    return fail(nullptr, SGP_EINVAL, "batch must be in [1, 65535] (got %d)", batch);
+  for (int a = 0; a < dim; ++a) {
+    if (!supported_n(n[a]))
+      return fail(nullptr, SGP_EINVAL,
+                  "n[%d] = %d not supported (2^a 3^b in {16..1024}, b <= 1)", a, n[a]);
+    if (!(L[a] > 0.0) || !std::isfinite(L[a]))
+      return fail(nullptr, SGP_EINVAL, "L[%d] must be positive and finite", a);
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(nullptr, SGP_EINVAL, "CUDA device %d not available", device);
+  DeviceGuard guard(device);
+  sgp_ctx* c = new sgp_ctx();
+  c->dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    c->n[a] = a < dim ? n[a] : 1;
+    c->L[a] = a < dim ? L[a] : 1.0;
+    c->h[a] = 2.0 * c->L[a] / c->n[a];
+  }
+  c->batch = batch;
+  c->prec = prec;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  c->ntot = (long long)c->n[0] * c->n[1] * c->n[2];
+  c->elem = prec == SGP_F32 ? 8 : 16;
+  c->prm.gx = c->prm.gy = c->prm.gz = 1.0;
+  auto bail = [&](sgp_status s, const char* what, cudaError_t e) {
+    fail(nullptr, s, "%s: %s", what, cudaGetErrorString(e));
+    sgp_destroy(c);
+    return s;
+  };
+  cudaError_t e;
+  const size_t fbytes = (size_t)batch * 5 * c->ntot * c->elem;
+  if ((e = cudaMalloc(&c->field, fbytes)) != cudaSuccess)
+    return bail(SGP_ENOMEM, "field allocation", e);
+  if ((e = cudaMemsetAsync(c->field, 0, fbytes, c->stream)) != cudaSuccess)
+    return bail(SGP_ECUDA, "field clear", e);
+  for (int a = 0; a < dim; ++a) {
+    if ((e = cudaMalloc(&c->tw[a], (size_t)c->n[a] * c->elem)) != cudaSuccess)
+      return bail(SGP_ENOMEM, "twiddle allocation", e);
+    if (prec == SGP_F32)
+      k_twiddles<float><<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (float2*)c->tw[a]);
+    else
+      k_twiddles<double><<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (double2*)c->tw[a]);
+    c->launches++;
+  }
+  if ((e = cudaMalloc(&c->t_dev, sizeof(double))) != cudaSuccess)
+    return bail(SGP_ENOMEM, "time allocation", e);
+  // observables scratch: the largest per-kernel partial array
+  const PassGeom gx = prec == SGP_F32 ? xpass_geom<float>(c->n[0]) : xpass_geom<double>(c->n[0]);
+  size_t need = (size_t)((c->n[1] * c->n[2] + gx.rows_or_tile - 1) / gx.rows_or_tile) * OBX_NT;
+  for (int a = 1; a < dim; ++a) {
+    const PassGeom gl = prec == SGP_F32 ? linepass_geom<float>(c->n[a]) : linepass_geom<double>(c->n[a]);
+    const size_t tiles = (size_t)(c->n[0] + gl.rows_or_tile - 1) / gl.rows_or_tile;
+    const size_t planes = a == 1 ? c->n[2] : c->n[1];
+    need = std::max(need, tiles * planes * OBL_NT);
+  }
+  c->partials_len = need * batch;
+  if ((e = cudaMalloc(&c->partials, c->partials_len * sizeof(double))) != cudaSuccess)
+    return bail(SGP_ENOMEM, "observables scratch", e);
+  if ((e = cudaMalloc(&c->obs_dev, (size_t)batch * OB_NT * sizeof(double))) != cudaSuccess)
+    return bail(SGP_ENOMEM, "observables output", e);
+  if ((e = cudaMemsetAsync(c->obs_dev, 0, (size_t)batch * OB_NT * sizeof(double), c->stream)) !=
+      cudaSuccess)
+    return bail(SGP_ECUDA, "observables clear", e);
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(SGP_ECUDA, "table launch", e);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(SGP_ECUDA, "create sync", e);
+  *out = c;
+  return SGP_OK;
+}
+
+sgp_status sgp_set_params(sgp_ctx* c, const sgp_params* p) {
+  if (!c) return SGP_EINVAL;
+  if (!p) return fail(c, SGP_EINVAL, "NULL params");
+  if (!finite_params(p)) return fail(c, SGP_EINVAL, "non-finite parameter");
+  DeviceGuard guard(c->device);
+  // tables depend on (Omega, gamma); they may still be in use by queued work
+  cudaStreamSynchronize(c->stream);
+  free_tables(c);
+  c->prm = *p;
+  c->have_params = true;
+  return SGP_OK;
+}
+
+sgp_status sgp_set_state(sgp_ctx* c, const void* src, int src_on_device, double t0) {
+  if (!c) return SGP_EINVAL;
+  if (!src) return fail(c, SGP_EINVAL, "NULL src");
+  if (!std::isfinite(t0)) return fail(c, SGP_EINVAL, "non-finite t0");
+  DeviceGuard guard(c->device);
+  const size_t bytes = (size_t)c->batch * 5 * c->ntot * c->elem;
+  SGP_CUDA(c, cudaMemcpyAsync(c->field, src, bytes,
+                              src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+  if (!src_on_device) SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->t = t0;
+  c->have_state = true;
+  return SGP_OK;
+}
+
+sgp_status sgp_get_state(sgp_ctx* c, void* dst, int dst_on_device) {
+  if (!c) return SGP_EINVAL;
+  if (!dst) return fail(c, SGP_EINVAL, "NULL dst");
+  DeviceGuard guard(c->device);
+  const size_t bytes = (size_t)c->batch * 5 * c->ntot * c->elem;
+  SGP_CUDA(c, cudaMemcpyAsync(dst, c->field, bytes,
+                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->stream));
+  if (!dst_on_device) SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SGP_OK;
+}
+
+sgp_status sgp_get_time(const sgp_ctx* c, double* t) {
+  if (!c || !t) return SGP_EINVAL;
+  *t = c->t;
+  return SGP_OK;
+}
+
+sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
+  if (!c) return SGP_EINVAL;
+  if (nsteps < 0) return fail(c, SGP_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SGP_EINVAL, "dt must be positive and finite");
+  if (scheme != SGP_TS2 && scheme != SGP_TS4) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
+  if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_step before sgp_set_state");
+  if (nsteps == 0) return SGP_OK;
+  DeviceGuard guard(c->device);
+  return c->prec == SGP_F32 ? run_steps<float>(c, nsteps, dt, scheme)
+                            : run_steps<double>(c, nsteps, dt, scheme);
+}
+
+sgp_status sgp_substep(sgp_ctx* c, int kind, double delta) {
+  if (!c) return SGP_EINVAL;
+  if (kind != SGP_SUB_NONLINEAR && kind != SGP_SUB_LINEAR)
+    return fail(c, SGP_EINVAL, "unknown substep kind %d", kind);
+  if (!std::isfinite(delta)) return fail(c, SGP_EINVAL, "non-finite delta");
+  if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_substep before sgp_set_state");
+  DeviceGuard guard(c->device);
+  return c->prec == SGP_F32 ? substep<float>(c, kind, delta) : substep<double>(c, kind, delta);
+}
+
+sgp_status sgp_observables(sgp_ctx* c, sgp_obs* out) {
+  if (!c) return SGP_EINVAL;
+  if (!out) return fail(c, SGP_EINVAL, "NULL out");
+  if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_observables before sgp_set_state");
+  DeviceGuard guard(c->device);
+  return c->prec == SGP_F32 ? observables<float>(c, out) : observables<double>(c, out);
+}
+
+sgp_status sgp_synchronize(sgp_ctx* c) {
+  if (!c) return SGP_EINVAL;
+  DeviceGuard guard(c->device);
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SGP_OK;
+}
+
+long long sgp_launch_count(const sgp_ctx* c) { return c ? c->launches : 0; }
+
+sgp_status sgp_destroy(sgp_ctx* c) {
+  if (!c) return SGP_OK;
+  DeviceGuard guard(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_tables(c);
+  cudaFree(c->field);
+  for (void* t : c->tw) cudaFree(t);
+  cudaFree(c->t_dev);
+  cudaFree(c->partials);
+  cudaFree(c->obs_dev);
+  delete c;
+  return SGP_OK;
+}
+
+}  // extern "C"

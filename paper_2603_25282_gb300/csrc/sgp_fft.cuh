@@ -1,0 +1,294 @@
+// sgp_fft.cuh -- complex helpers and the in-CTA line FFT used by every pass.
+//
+// The discrete transforms are those of Sec. 3.1 (forward with the kernel
+// exp(-2 pi i p j / N), inverse with exp(+2 pi i p j / N)); normalisation is
+// not applied here (the 1/N factors are folded into the per-mode tables).
+//
+// Line FFT scheme: a line of N complex values is owned by T = N/E threads;
+// thread i holds elements i + T*c (c = 0..E-1) in registers ("layout A").
+// Each Stockham radix stage (radix RD, span NS = product of earlier radices)
+// reads its butterfly inputs straight from layout A (butterfly b = i + T*k
+// takes elements b + r*N/RD = i + T*(k + r*E/RD)), applies the twiddles
+// exp(-+2 pi i (b mod NS) r / (NS*RD)), does the RD-point DFT and scatters to
+// (b div NS)*NS*RD + (b mod NS) + r*NS; a shared-memory exchange brings the
+// data back to layout A.  The last stage's scatter is layout A itself, so a
+// transform of S stages needs S-1 exchanges and leaves the result in natural
+// order in the same layout as its input.
+//
+// All five components of a point live in the same thread, which lets the
+// pointwise nonlinear flow and the per-mode 5x5 mix run on registers between
+// two transforms.  The stage twiddles are formed once per stage and reused
+// for the five components; exchanges alternate between two buffers so that
+// one __syncthreads per component and stage suffices.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgp {
+
+// ----------------------------------------------------------------------------
+// complex helpers (float2 / double2)
+// ----------------------------------------------------------------------------
+template <typename R> struct cplx_t;
+template <> struct cplx_t<float> { typedef float2 type; };
+template <> struct cplx_t<double> { typedef double2 type; };
+template <typename R> using cplx = typename cplx_t<R>::type;
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mkc(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cneg(C a) { return mkc(-a.x, -a.y); }
+// a * b
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mkc(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mkc(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+template <typename C> __device__ __forceinline__ C cconjmul(C a, C b) {
+  return mkc(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return mkc(a.x * s, a.y * s); }
+// i * a and -i * a
+template <typename C> __device__ __forceinline__ C cmuli(C a) { return mkc(-a.y, a.x); }
+template <typename C> __device__ __forceinline__ C cmulmi(C a) { return mkc(a.y, -a.x); }
+// acc + a * s (s real)
+template <typename C, typename R> __device__ __forceinline__ C caxpy(C acc, C a, R s) {
+  return mkc(fma(a.x, s, acc.x), fma(a.y, s, acc.y));
+}
+template <typename C> __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x) {
+  return fma(a.x, a.x, a.y * a.y);
+}
+
+// ----------------------------------------------------------------------------
+// radix plans
+// ----------------------------------------------------------------------------
+// Radix of stage s for a length-N line with E elements per thread: greedy over
+// {8, 6, 4, 3, 2}, each radix dividing both E and what is left of N.  Returns
+// 0 past the last stage.
+__host__ __device__ constexpr int radix_at(int N, int E, int s) {
+  int rem = N;
+  for (int k = 0; k <= s; ++k) {
+    if (rem == 1) return 0;
+    int r = 0;
+    if (E % 8 == 0 && rem % 8 == 0) r = 8;
+    else if (E % 6 == 0 && rem % 6 == 0) r = 6;
+    else if (E % 4 == 0 && rem % 4 == 0) r = 4;
+    else if (E % 3 == 0 && rem % 3 == 0) r = 3;
+    else if (E % 2 == 0 && rem % 2 == 0) r = 2;
+    else return -1;  // no plan: rejected at compile time below
+    if (k == s) return r;
+    rem /= r;
+  }
+  return 0;
+}
+
+__host__ __device__ constexpr bool plan_ok(int N, int E) {
+  if (N % E) return false;
+  int s = 0, prod = 1;
+  while (true) {
+    int r = radix_at(N, E, s);
+    if (r < 0) return false;
+    if (r == 0) break;
+    prod *= r;
+    ++s;
+  }
+  return prod == N;
+}
+
+__host__ __device__ constexpr int num_stages(int N, int E) {
+  int s = 0;
+  while (radix_at(N, E, s) > 0) ++s;
+  return s;
+}
+
+// Shared-memory padding: one element every 128 bytes breaks the power-of-two
+// strides of the early stages across banks.
+template <typename R> struct PadShift;
+template <> struct PadShift<float> { static constexpr int value = 4; };
+template <> struct PadShift<double> { static constexpr int value = 3; };
+template <typename R> __device__ __forceinline__ int padx(int idx) {
+  return idx + (idx >> PadShift<R>::value);
+}
+// Padded line length (+1 so that consecutive lines start in different banks).
+template <typename R> __host__ __device__ constexpr int line_pad(int N) {
+  return N + (N >> PadShift<R>::value) + 1;
+}
+
+// ----------------------------------------------------------------------------
+// small DFTs, DIR = -1 forward, +1 inverse
+// ----------------------------------------------------------------------------
+template <int DIR, typename C> __device__ __forceinline__ C rot_mi(C a) {
+  // multiply by -i (forward) or +i (inverse)
+  return DIR < 0 ? cmulmi(a) : cmuli(a);
+}
+
+template <int RD, int DIR, typename C> struct Dft;
+
+template <int DIR, typename C> struct Dft<2, DIR, C> {
+  __device__ __forceinline__ static void run(C (&x)[2]) {
+    C a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  }
+};
+
+template <int DIR, typename C> struct Dft<4, DIR, C> {
+  __device__ __forceinline__ static void run(C (&x)[4]) {
+    C t0 = cadd(x[0], x[2]), t1 = csub(x[0], x[2]);
+    C t2 = cadd(x[1], x[3]), t3 = rot_mi<DIR>(csub(x[1], x[3]));
+    x[0] = cadd(t0, t2);
+    x[2] = csub(t0, t2);
+    x[1] = cadd(t1, t3);
+    x[3] = csub(t1, t3);
+  }
+};
+
+template <int DIR, typename C> struct Dft<8, DIR, C> {
+  __device__ __forceinline__ static void run(C (&x)[8]) {
+    typedef decltype(x[0].x) R;
+    const R h = (R)0.70710678118654752440;
+    C e[4] = {x[0], x[2], x[4], x[6]};
+    C o[4] = {x[1], x[3], x[5], x[7]};
+    Dft<4, DIR, C>::run(e);
+    Dft<4, DIR, C>::run(o);
+    // twiddles W8^k, k = 1..3 (forward: (1-i)/sqrt2, -i, (-1-i)/sqrt2)
+    C o1 = o[1], o2 = o[2], o3 = o[3];
+    if (DIR < 0) {
+      o1 = mkc((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+      o2 = cmulmi(o2);
+      o3 = mkc((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+    } else {
+      o1 = mkc((o1.x - o1.y) * h, (o1.y + o1.x) * h);
+      o2 = cmuli(o2);
+      o3 = mkc(-(o3.x + o3.y) * h, (o3.x - o3.y) * h);
+    }
+    x[0] = cadd(e[0], o[0]);
+    x[4] = csub(e[0], o[0]);
+    x[1] = cadd(e[1], o1);
+    x[5] = csub(e[1], o1);
+    x[2] = cadd(e[2], o2);
+    x[6] = csub(e[2], o2);
+    x[3] = cadd(e[3], o3);
+    x[7] = csub(e[3], o3);
+  }
+};
+
+template <int DIR, typename C> struct Dft<3, DIR, C> {
+  __device__ __forceinline__ static void run(C (&x)[3]) {
+    typedef decltype(x[0].x) R;
+    const R s3 = (R)0.86602540378443864676;
+    C t = cadd(x[1], x[2]);
+    C u = csub(x[1], x[2]);
+    C m = mkc(fma(t.x, (R)-0.5, x[0].x), fma(t.y, (R)-0.5, x[0].y));
+    // forward: X1 = m - i s3 u, X2 = m + i s3 u
+    C iu = DIR < 0 ? mkc(u.y * s3, -u.x * s3) : mkc(-u.y * s3, u.x * s3);
+    x[0] = cadd(x[0], t);
+    x[1] = cadd(m, iu);
+    x[2] = csub(m, iu);
+  }
+};
+
+template <int DIR, typename C> struct Dft<6, DIR, C> {
+  __device__ __forceinline__ static void run(C (&x)[6]) {
+    typedef decltype(x[0].x) R;
+    const R s3 = (R)0.86602540378443864676;
+    C e[3] = {x[0], x[2], x[4]};
+    C o[3] = {x[1], x[3], x[5]};
+    Dft<3, DIR, C>::run(e);
+    Dft<3, DIR, C>::run(o);
+    // W6^1 = 1/2 -+ i s3, W6^2 = -1/2 -+ i s3
+    const R sg = DIR < 0 ? (R)-1 : (R)1;
+    C w1 = mkc((R)0.5, sg * s3), w2 = mkc((R)-0.5, sg * s3);
+    C o1 = cmul(o[1], w1), o2 = cmul(o[2], w2);
+    x[0] = cadd(e[0], o[0]);
+    x[3] = csub(e[0], o[0]);
+    x[1] = cadd(e[1], o1);
+    x[4] = csub(e[1], o1);
+    x[2] = cadd(e[2], o2);
+    x[5] = csub(e[2], o2);
+  }
+};
+
+// ----------------------------------------------------------------------------
+// Stockham stages over NC components held in registers
+// ----------------------------------------------------------------------------
+// v[c][e]: element i + T*e of component c's line.  tw: W_N^k = exp(-2 pi i k/N),
+// k = 0..N-1, in shared memory.  b0/b1: two padded exchange lines of this
+// thread group.  DIR = -1 forward, +1 inverse.  Every thread of the CTA must
+// call this (it contains __syncthreads).
+template <typename R, int N, int E, int DIR, int NC, int S, int NS>
+struct FftStages {
+  typedef cplx<R> C;
+  __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const C* tw,
+                                             C* b0, C* b1) {
+    constexpr int RD = radix_at(N, E, S);
+    if constexpr (RD > 0) {
+      constexpr int T = N / E;
+      constexpr int B = E / RD;
+      constexpr bool LAST = (NS * RD == N);
+      constexpr int TSTEP = N / (NS * RD);
+      C w[B][RD];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        w[k][0] = mkc((R)1, (R)0);
+        if constexpr (NS > 1) {
+          const int j = (i + T * k) % NS;
+#pragma unroll
+          for (int r = 1; r < RD; ++r) {
+            C t = tw[j * r * TSTEP];
+            w[k][r] = DIR < 0 ? t : cconj(t);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        C* buf = ((S * NC + c) & 1) ? b1 : b0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          C x[RD];
+#pragma unroll
+          for (int r = 0; r < RD; ++r) {
+            x[r] = v[c][k + r * B];
+            if constexpr (NS > 1) {
+              if (r > 0) x[r] = cmul(x[r], w[k][r]);
+            }
+          }
+          Dft<RD, DIR, C>::run(x);
+          if constexpr (LAST) {
+#pragma unroll
+            for (int r = 0; r < RD; ++r) v[c][k + r * B] = x[r];
+          } else {
+            const int b = i + T * k;
+            const int idxD = (b / NS) * NS * RD + (b % NS);
+#pragma unroll
+            for (int r = 0; r < RD; ++r) buf[padx<R>(idxD + r * NS)] = x[r];
+          }
+        }
+        if constexpr (!LAST) {
+          __syncthreads();
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[c][e] = buf[padx<R>(i + T * e)];
+        }
+      }
+      FftStages<R, N, E, DIR, NC, S + 1, NS * RD>::run(v, i, tw, b0, b1);
+    }
+  }
+};
+
+template <typename R, int N, int E, int DIR, int NC>
+__device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i,
+                                          const cplx<R>* tw, cplx<R>* b0,
+                                          cplx<R>* b1) {
+  static_assert(plan_ok(N, E), "no radix plan for this (N, E)");
+  // the previous user of the exchange buffers may still be reading
+  __syncthreads();
+  FftStages<R, N, E, DIR, NC, 0, 1>::run(v, i, tw, b0, b1);
+}
+
+}  // namespace sgp

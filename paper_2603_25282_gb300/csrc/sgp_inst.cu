@@ -1,0 +1,172 @@
+// sgp_inst.cu -- explicit instantiation of the pass kernels and their
+// launchers for one precision (SGP_REAL) and one kernel family (SGP_PART:
+// 0 = x-lines, 1 = strided lines).  Built several times with different
+// macros so that the instantiations compile in parallel.
+#include "sgp_launch.cuh"
+
+#ifndef SGP_REAL
+#error "define SGP_REAL (float or double)"
+#endif
+#ifndef SGP_PART
+#error "define SGP_PART (0 or 1)"
+#endif
+
+namespace sgp {
+
+namespace {
+// Opt in to more than 48 KB of dynamic shared memory once per device.
+template <typename K>
+cudaError_t prepare(K kern, size_t smem, int* done_dev) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (*done_dev == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) *done_dev = dev;
+  return e;
+}
+}  // namespace
+
+typedef SGP_REAL Real;
+
+#if SGP_PART == 0
+
+template <>
+PassGeom xpass_geom<Real>(int N) {
+  switch (N) {
+#define SGP_CASE(NN)                                                        \
+  case NN: {                                                                \
+    typedef XCfg<Real, NN, elems_per_thread<Real, NN>()> Cfg;               \
+    return PassGeom{Cfg::THREADS, Cfg::ROWS, Cfg::SMEM};                    \
+  }
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return PassGeom{0, 0, 0};
+  }
+}
+
+template <int N>
+static cudaError_t xpass_n(const XPassArgs<Real>& a, int members, cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef XCfg<Real, N, E> Cfg;
+  static int done = -1;
+  cudaError_t e = prepare(k_xpass<Real, N, E>, Cfg::SMEM, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.rows + Cfg::ROWS - 1) / Cfg::ROWS, members);
+  k_xpass<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_xpass<Real>(int N, const XPassArgs<Real>& a, int members, cudaStream_t s) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return xpass_n<NN>(a, members, s);
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+static cudaError_t obs_x_n(const ObsXArgs<Real>& a, int members, cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef XCfg<Real, N, E> Cfg;
+  static int done = -1;
+  cudaError_t e = prepare(k_obs_x<Real, N, E>, Cfg::SMEM, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.rows + Cfg::ROWS - 1) / Cfg::ROWS, members);
+  k_obs_x<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_obs_x<Real>(int N, const ObsXArgs<Real>& a, int members, cudaStream_t s) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return obs_x_n<NN>(a, members, s);
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+#else  // SGP_PART == 1
+
+template <>
+PassGeom linepass_geom<Real>(int N) {
+  switch (N) {
+#define SGP_CASE(NN)                                                        \
+  case NN: {                                                                \
+    typedef LCfg<Real, NN, elems_per_thread<Real, NN>()> Cfg;               \
+    return PassGeom{Cfg::THREADS, Cfg::TILE, Cfg::SMEM};                    \
+  }
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return PassGeom{0, 0, 0};
+  }
+}
+
+template <int N>
+static cudaError_t linepass_n(const LPassArgs<Real>& a, int planes, int members,
+                              cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef LCfg<Real, N, E> Cfg;
+  static int done = -1;
+  cudaError_t e = prepare(k_linepass<Real, N, E>, Cfg::SMEM, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
+  k_linepass<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_linepass<Real>(int N, const LPassArgs<Real>& a, int planes, int members,
+                                  cudaStream_t s) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return linepass_n<NN>(a, planes, members, s);
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+static cudaError_t obs_line_n(const ObsLArgs<Real>& a, int planes, int members,
+                              cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef LCfg<Real, N, E> Cfg;
+  static int done = -1;
+  cudaError_t e = prepare(k_obs_line<Real, N, E>, Cfg::SMEM, &done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
+  k_obs_line<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_obs_line<Real>(int N, const ObsLArgs<Real>& a, int planes, int members,
+                                  cudaStream_t s) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return obs_line_n<NN>(a, planes, members, s);
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+#endif
+
+}  // namespace sgp

@@ -1,0 +1,647 @@
+// sgp_kernels.cuh -- pass kernels of the compact splitting propagator.
+//
+// Two kinds of passes stream the field once each (read + write):
+//   x-pass   : contiguous x-lines of all five components of one grid row;
+//              optional inverse x-FFT, the exact nonlinear flow (Eq.
+//              (solution2)) at every point, optional forward x-FFT.
+//   line pass: strided lines (y, or z in 3D) over a tile of consecutive x
+//              positions; optional forward FFT, the per-mode linear flow
+//              exp(-i|nu|^2 d/2) exp(i d Q) (Eq. (sl1)), optional inverse FFT.
+// Between passes the field stays in a mixed representation (transformed
+// along the axes already done), so a TS2 step in 2D is one x-pass and one
+// line pass.
+//
+// The per-mode 5x5 matrix exp(i d Q) is never stored: Q = lambda n.f with
+// lambda = sqrt(Omega^2 + gamma^2 |nu_perp|^2) (Sec. 3.1; the eigenvalues of Q
+// are lambda*{-2..2}), so exp(i d Q) is the spin-2 image of the SU(2) matrix
+// U = exp(i d lambda n.sigma/2).  Writing U11 = cp*ahat, U12 = sp*bhat (cp, sp
+// real, ahat, bhat unit), the spin-2 image factors as
+// diag(w^m) d(cp, sp) diag(z^m), w = ahat*bhat, z = ahat*conj(bhat),
+// m = 2..-2, with d the real spin-2 rotation matrix below.  The same
+// factorisation gives exp(-i c1 d F.f) of Eq. (solution2).
+#pragma once
+#include "sgp_fft.cuh"
+
+namespace sgp {
+
+// x-pass mode bits
+enum { XP_INV = 1, XP_NL = 2, XP_FWD = 4 };
+// line-pass mode bits
+enum { LP_FWD = 1, LP_MIX = 2, LP_INV = 4 };
+
+template <typename R>
+struct XPassArgs {
+  cplx<R>* field;        // [batch][5][ntot]
+  const cplx<R>* tw;     // W_Nx^k, k < Nx
+  long long ntot;        // nx*ny*nz
+  int rows;              // ny*nz rows per member
+  int ny;
+  int mode;
+  R x0, hx, y0, hy, z0, hz;      // coordinates x_j = x0 + j*hx
+  // nonlinear flow over delta at time t = *t_base + t_off
+  R delta, c0p, c1, c2, gx2h, gy2h, gz2h;
+  double omega;
+  const double* t_base;
+  double t_off;
+};
+
+template <typename R>
+struct LPassArgs {
+  cplx<R>* field;
+  const cplx<R>* tw;          // W_N^k along the line axis
+  long long ntot;
+  int nx;                     // number of x positions (tile axis)
+  long long line_stride;      // element stride along the line
+  long long plane_stride;     // element stride between planes (blockIdx.y)
+  int mode;
+  int axis;                   // 1: lines along y (2D); 2: lines along z (3D)
+  int NX, NY;                 // grid sizes along x and y (mode indices)
+  const R* lam;               // [(NX/2+1)*(NY/2+1)][4]: ahat.re, ahat.im, cp, sp
+  const cplx<R>* kx;          // exp(-i nu_x^2 d/2)/NX etc.
+  const cplx<R>* ky;
+  const cplx<R>* kz;
+  R pix, piy;                 // pi/Lx, pi/Ly
+};
+
+// ----------------------------------------------------------------------------
+// spin-2 image of an SU(2) element in the factorised form
+// ----------------------------------------------------------------------------
+// v <- K * diag(w^m) d(cp, sp) diag(z^m) v, m = 2, 1, 0, -1, -2.
+template <typename R>
+__device__ __forceinline__ void apply_spin2(cplx<R> (&v)[5], cplx<R> ahat,
+                                            cplx<R> bhat, R cp, R sp,
+                                            cplx<R> K) {
+  typedef cplx<R> C;
+  const R r6 = (R)2.44948974278317809820;   // sqrt(6)
+  const C w = cmul(ahat, bhat);
+  const C z = cmulc(ahat, bhat);
+  const C z2 = cmul(z, z);
+  // u = diag(z^m) v
+  C u0 = cmul(z2, v[0]);
+  C u1 = cmul(z, v[1]);
+  C u2 = v[2];
+  C u3 = cmulc(v[3], z);
+  C u4 = cmulc(v[4], z2);
+  // real spin-2 rotation matrix d(c, s) (rows/cols m = 2..-2)
+  const R c = cp, s = sp;
+  const R c2 = c * c, s2 = s * s, cs = c * s;
+  const R A = c2 * c2, B = s2 * s2;
+  const R P = (R)2 * c2 * cs;        // 2 c^3 s
+  const R Qv = (R)2 * cs * s2;       // 2 c s^3
+  const R Rv = r6 * c2 * s2;         // sqrt6 c^2 s^2
+  const R Sv = r6 * cs * (c2 - s2);  // sqrt6 c s (c^2 - s^2)
+  const R T1 = c2 * (c2 - (R)3 * s2);
+  const R T2 = s2 * ((R)3 * c2 - s2);
+  const R M0 = A + B - (R)4 * c2 * s2;
+  C o0 = cscale(u0, A);
+  o0 = caxpy(o0, u1, P);
+  o0 = caxpy(o0, u2, Rv);
+  o0 = caxpy(o0, u3, Qv);
+  o0 = caxpy(o0, u4, B);
+  C o1 = cscale(u0, -P);
+  o1 = caxpy(o1, u1, T1);
+  o1 = caxpy(o1, u2, Sv);
+  o1 = caxpy(o1, u3, T2);
+  o1 = caxpy(o1, u4, Qv);
+  C o2 = cscale(u0, Rv);
+  o2 = caxpy(o2, u1, -Sv);
+  o2 = caxpy(o2, u2, M0);
+  o2 = caxpy(o2, u3, Sv);
+  o2 = caxpy(o2, u4, Rv);
+  C o3 = cscale(u0, -Qv);
+  o3 = caxpy(o3, u1, T2);
+  o3 = caxpy(o3, u2, -Sv);
+  o3 = caxpy(o3, u3, T1);
+  o3 = caxpy(o3, u4, P);
+  C o4 = cscale(u0, B);
+  o4 = caxpy(o4, u1, -Qv);
+  o4 = caxpy(o4, u2, Rv);
+  o4 = caxpy(o4, u3, -P);
+  o4 = caxpy(o4, u4, A);
+  // v = K diag(w^m) o
+  const C Kw = cmul(K, w);
+  const C Kw2 = cmul(Kw, w);
+  const C Kwc = cmulc(K, w);
+  const C Kwc2 = cmulc(Kwc, w);
+  v[0] = cmul(Kw2, o0);
+  v[1] = cmul(Kw, o1);
+  v[2] = cmul(K, o2);
+  v[3] = cmul(Kwc, o3);
+  v[4] = cmul(Kwc2, o4);
+}
+
+__device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sincos(a, s, c); }
+__device__ __forceinline__ float rsqrt_r(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double rsqrt_r(double a) { return rsqrt(a); }
+
+// unit complex in the direction of u (1 if u == 0) and |u|
+template <typename C, typename R>
+__device__ __forceinline__ C unit_dir(C u, R& mag) {
+  const R m2 = cabs2(u);
+  if (m2 > (R)0) {
+    const R ri = rsqrt_r(m2);
+    mag = m2 * ri;
+    return mkc(u.x * ri, u.y * ri);
+  }
+  mag = (R)0;
+  return mkc((R)1, (R)0);
+}
+
+// ----------------------------------------------------------------------------
+// exact nonlinear flow at one point (Sec. 3.2, Eq. (solution2))
+// ----------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
+                                                R c0p, R c1, R c2) {
+  typedef cplx<R> C;
+  const R r6 = (R)2.44948974278317809820;
+  const R rs5 = (R)0.44721359549995793928;   // 1/sqrt(5)
+  const R a0 = cabs2(v[0]), a1 = cabs2(v[1]), a2 = cabs2(v[2]);
+  const R a3 = cabs2(v[3]), a4 = cabs2(v[4]);
+  const R rho = a0 + a1 + a2 + a3 + a4;
+  const R Fz = (R)2 * (a0 - a4) + a1 - a3;
+  // F_+ = 2(conj(p2) p1 + conj(m1) m2) + sqrt6 (conj(p1) p0 + conj(p0) m1)
+  C Fp = cscale(cadd(cconjmul(v[0], v[1]), cconjmul(v[3], v[4])), (R)2);
+  Fp = cadd(Fp, cscale(cadd(cconjmul(v[1], v[2]), cconjmul(v[2], v[3])), r6));
+  // A00 = (2 p2 m2 - 2 p1 m1 + p0^2)/sqrt5
+  C A00 = csub(cmul(v[0], v[4]), cmul(v[1], v[3]));
+  A00 = cscale(cadd(cscale(A00, (R)2), cmul(v[2], v[2])), rs5);
+  // singlet-pair rotation: cos(c2 S d) Psi + i sin(c2 S d)/S (rho/5 Psi - A00 A conj(Psi))
+  const R S2 = rho * rho * (R)0.04 - cabs2(A00) * (R)0.2;
+  const R S = S2 > (R)0 ? sqrt(S2) : (R)0;
+  R sn, cs;
+  sincos_r(c2 * S * delta, &sn, &cs);
+  const R sinc = S > (R)0 ? sn / S : c2 * delta;
+  const R r5 = rho * (R)0.2;
+  // A conj(Psi) = (conj m2, -conj m1, conj p0, -conj p1, conj p2)/sqrt5
+  const C As = cscale(A00, rs5);
+  C b[5];
+  {
+    const C ac[5] = {cconj(v[4]), cneg(cconj(v[3])), cconj(v[2]),
+                     cneg(cconj(v[1])), cconj(v[0])};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      C t = csub(cscale(v[k], r5), cmul(As, ac[k]));    // rho/5 Psi - A00 A conj(Psi)
+      t = cscale(cmuli(t), sinc);
+      b[k] = cadd(cscale(v[k], cs), t);
+    }
+  }
+  // spin rotation exp(-i c1 d F.f) = spin-2 image of cos(k/2) - i sin(k/2) Fhat.sigma,
+  // k = c1 d |F|:  U11 = cos(k/2) - i q Fz, U12 = -i q conj(F+), q = sin(k/2)/|F|
+  const R F2 = cabs2(Fp) + Fz * Fz;
+  R q, ch;
+  if (F2 > (R)0) {
+    const R Fn = sqrt(F2);
+    R sh;
+    sincos_r((R)0.5 * c1 * delta * Fn, &sh, &ch);
+    q = sh / Fn;
+  } else {
+    ch = (R)1;
+    q = (R)0;
+  }
+  const C U11 = mkc(ch, -q * Fz);
+  const C U12 = mkc(-q * Fp.y, -q * Fp.x);
+  R cp, sp;
+  const C ahat = unit_dir(U11, cp);
+  const C bhat = unit_dir(U12, sp);
+  // scalar phase exp(-i d (V + (c0 + c2/5) rho))
+  R ps, pc;
+  sincos_r(-delta * (V + c0p * rho), &ps, &pc);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k] = b[k];
+  apply_spin2<R>(v, ahat, bhat, cp, sp, mkc(pc, ps));
+}
+
+// ----------------------------------------------------------------------------
+// x-pass kernel
+// ----------------------------------------------------------------------------
+template <typename R, int N, int E>
+struct XCfg {
+  static constexpr int T = N / E;
+  static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
+  static constexpr int THREADS = ROWS * T;
+  static constexpr int LP = line_pad<R>(N);
+  static constexpr size_t SMEM = sizeof(cplx<R>) * (size_t)(N + 2 * ROWS * LP);
+};
+
+template <typename R, int N, int E>
+__global__ void __launch_bounds__(XCfg<R, N, E>::THREADS)
+k_xpass(XPassArgs<R> a) {
+  typedef cplx<R> C;
+  typedef XCfg<R, N, E> Cfg;
+  constexpr int T = Cfg::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* xb = tw + N;
+  __shared__ R s_rot[2];
+  const int g = threadIdx.x / T;
+  const int i = threadIdx.x - g * T;
+  for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
+  if ((a.mode & XP_NL) && threadIdx.x == 0) {
+    const double t = *a.t_base + a.t_off;
+    double sn, cs;
+    sincos(a.omega * t, &sn, &cs);
+    s_rot[0] = (R)cs;
+    s_rot[1] = (R)sn;
+  }
+  const int row = blockIdx.x * Cfg::ROWS + g;
+  const bool valid = row < a.rows;
+  C* base = a.field + (size_t)blockIdx.y * 5 * a.ntot + (size_t)(valid ? row : 0) * N + i;
+  C v[5][E];
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
+  C* b0 = xb + g * Cfg::LP;
+  C* b1 = xb + (Cfg::ROWS + g) * Cfg::LP;
+  if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  if (a.mode & XP_NL) {
+    __syncthreads();   // s_rot
+    const R co = s_rot[0], si = s_rot[1];
+    const int ky = row % a.ny;
+    const int kz = row / a.ny;
+    const R y = a.y0 + (R)ky * a.hy;
+    const R z = a.z0 + (R)kz * a.hz;
+    const R vz = a.gz2h * z * z;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const R x = a.x0 + (R)(i + T * e) * a.hx;
+      const R xr = co * x + si * y;
+      const R yr = co * y - si * x;
+      const R V = a.gx2h * xr * xr + a.gy2h * yr * yr + vz;
+      C p[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
+      nonlinear_point<R>(p, V, a.delta, a.c0p, a.c1, a.c2);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c][e] = p[c];
+    }
+  }
+  if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) base[(size_t)c * a.ntot + T * e] = v[c][e];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// line-pass kernel (strided lines, tile of TILE consecutive x positions)
+// ----------------------------------------------------------------------------
+template <typename R, int N, int E>
+struct LCfg {
+  static constexpr int T = N / E;
+  static constexpr int TMAX = sizeof(R) == 4 ? 32 : 16;
+  static constexpr int TMIN = sizeof(R) == 4 ? 4 : 2;
+  static constexpr int TILE = (512 / T) > TMAX ? TMAX : ((512 / T) < TMIN ? TMIN : (512 / T));
+  static constexpr int THREADS = TILE * T;
+  static constexpr int LP = line_pad<R>(N);
+  static constexpr size_t SMEM = sizeof(cplx<R>) * (size_t)(N + 2 * TILE * LP);
+};
+
+template <typename R>
+__device__ __forceinline__ void load_lam(const R* lam, int idx, R& ar, R& ai, R& cp, R& sp);
+template <>
+__device__ __forceinline__ void load_lam<float>(const float* lam, int idx, float& ar,
+                                                float& ai, float& cp, float& sp) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(lam) + idx);
+  ar = t.x; ai = t.y; cp = t.z; sp = t.w;
+}
+template <>
+__device__ __forceinline__ void load_lam<double>(const double* lam, int idx, double& ar,
+                                                 double& ai, double& cp, double& sp) {
+  const double2 t0 = __ldg(reinterpret_cast<const double2*>(lam) + 2 * idx);
+  const double2 t1 = __ldg(reinterpret_cast<const double2*>(lam) + 2 * idx + 1);
+  ar = t0.x; ai = t0.y; cp = t1.x; sp = t1.y;
+}
+
+// linear flow of one Fourier mode (p, q, r in FFT order)
+template <typename R>
+__device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
+                                         int p, int q, int r) {
+  typedef cplx<R> C;
+  const int ps = p < a.NX / 2 ? p : p - a.NX;
+  const int qs = q < a.NY / 2 ? q : q - a.NY;
+  const int aps = ps < 0 ? -ps : ps;
+  const int aqs = qs < 0 ? -qs : qs;
+  R ar, ai, cp, sp;
+  load_lam<R>(a.lam, aps * (a.NY / 2 + 1) + aqs, ar, ai, cp, sp);
+  // bhat = (nu_x - i nu_y)/|nu_perp|
+  R mag;
+  const C bhat = unit_dir(mkc((R)ps * a.pix, -(R)qs * a.piy), mag);
+  C K = cmul(__ldg(a.kx + p), __ldg(a.ky + q));
+  if (a.axis == 2) K = cmul(K, __ldg(a.kz + r));
+  apply_spin2<R>(v, mkc(ar, ai), bhat, cp, sp, K);
+}
+
+template <typename R, int N, int E>
+__global__ void __launch_bounds__(LCfg<R, N, E>::THREADS)
+k_linepass(LPassArgs<R> a) {
+  typedef cplx<R> C;
+  typedef LCfg<R, N, E> Cfg;
+  constexpr int T = Cfg::T;
+  constexpr int TILE = Cfg::TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* xb = tw + N;
+  const int col = threadIdx.x % TILE;
+  const int i = threadIdx.x / TILE;
+  for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
+  const int xcol = blockIdx.x * TILE + col;
+  const bool valid = xcol < a.nx;
+  C* base = a.field + (size_t)blockIdx.z * 5 * a.ntot + (size_t)blockIdx.y * a.plane_stride +
+            (valid ? xcol : 0) + (size_t)i * a.line_stride;
+  const size_t step = (size_t)T * a.line_stride;
+  C v[5][E];
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      v[c][e] = valid ? base[(size_t)c * a.ntot + e * step] : mkc((R)0, (R)0);
+  C* b0 = xb + col * Cfg::LP;
+  C* b1 = xb + (TILE + col) * Cfg::LP;
+  if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+  if (a.mode & LP_MIX) {
+    const int pm = valid ? xcol : 0;   // idle threads of a ragged tile read mode 0
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int pos = i + T * e;
+      C p5[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
+      if (a.axis == 1)
+        mix_mode<R>(p5, a, pm, pos, 0);
+      else
+        mix_mode<R>(p5, a, pm, blockIdx.y, pos);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
+    }
+  }
+  if (a.mode & LP_INV) fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) base[(size_t)c * a.ntot + e * step] = v[c][e];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// observables (Sec. 2), FP64 sums
+// ----------------------------------------------------------------------------
+// term indices of the per-member sums
+enum {
+  OB_M0 = 0,     // 0..4 component masses
+  OB_WX = 5, OB_WY = 6, OB_WZ = 7,
+  OB_POT = 8, OB_INT = 9,
+  OB_KX = 10, OB_LZX = 11, OB_SOCX = 12,
+  OB_KY = 13, OB_LZY = 14, OB_SOCY = 15,
+  OB_KZ = 16,
+  OB_NT = 19      // (the z-line kernel also writes two unused slots after OB_KZ)
+};
+
+struct ObsArgsBase {
+  long long ntot;
+  int rows, ny;
+  double x0, hx, y0, hy, z0, hz;
+  double omega, t;
+  double c0, c1, c2, gx2h, gy2h, gz2h;
+  double* partials;      // [member][nblocks][terms of the kernel]
+  int nblocks;           // blocks per member
+};
+
+constexpr int OBX_NT = 13;   // terms written by k_obs_x  (OB_M0 .. OB_SOCX)
+constexpr int OBL_NT = 3;    // terms written by k_obs_line (kin, lz, soc)
+
+template <typename R>
+struct ObsXArgs : ObsArgsBase {
+  const cplx<R>* field;
+  const cplx<R>* tw;
+  R dnu;                 // pi/Lx / Nx (derivative factor with the 1/N of the forward transform)
+  int NX;
+};
+
+template <typename R>
+struct ObsLArgs : ObsArgsBase {
+  const cplx<R>* field;
+  const cplx<R>* tw;
+  int nx;
+  long long line_stride, plane_stride;
+  int axis;              // 1: y lines, 2: z lines
+  R dnu;                 // pi/L / N along the line axis
+  int NL;                // line length
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block reduction of NTERM sums; thread 0 writes them to out[0..NTERM-1].
+template <int NTERM>
+__device__ __forceinline__ void block_sums(double (&acc)[NTERM], double* out, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NTERM; ++k) {
+    const double s = warp_sum(acc[k]);
+    if (lane == 0) red[warp * NTERM + k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NTERM) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * NTERM + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// x-lines: pointwise terms and the x-derivative terms.
+template <typename R, int N, int E>
+__global__ void __launch_bounds__(XCfg<R, N, E>::THREADS)
+k_obs_x(ObsXArgs<R> a) {
+  typedef cplx<R> C;
+  typedef XCfg<R, N, E> Cfg;
+  constexpr int T = Cfg::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* xb = tw + N;
+  __shared__ double red[32 * 10];
+  const int g = threadIdx.x / T;
+  const int i = threadIdx.x - g * T;
+  for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
+  const int row = blockIdx.x * Cfg::ROWS + g;
+  const bool valid = row < a.rows;
+  const C* base = a.field + (size_t)blockIdx.y * 5 * a.ntot + (size_t)(valid ? row : 0) * N + i;
+  C v[5][E];
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
+  C* b0 = xb + g * Cfg::LP;
+  C* b1 = xb + (Cfg::ROWS + g) * Cfg::LP;
+  fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = i + T * e;
+    const int ps = p < N / 2 ? p : p - N;
+    const R f = (R)ps * a.dnu;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c][e] = cscale(cmuli(v[c][e]), f);
+  }
+  fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  double acc[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) acc[k] = 0.0;
+  if (valid) {
+    const double co = cos(a.omega * a.t), si = sin(a.omega * a.t);
+    const int ky = row % a.ny, kz = row / a.ny;
+    const double y = a.y0 + ky * a.hy, z = a.z0 + kz * a.hz;
+    const double s6h = 1.22474487139158904910, s6 = 2.44948974278317809820;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const double x = a.x0 + (i + T * e) * a.hx;
+      double re[5], im[5], dr[5], di[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const C u = base[(size_t)c * a.ntot + T * e];
+        re[c] = (double)u.x; im[c] = (double)u.y;
+        dr[c] = (double)v[c][e].x; di[c] = (double)v[c][e].y;
+      }
+      double m[5], rho = 0.0, kin = 0.0, lzi = 0.0;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        m[c] = re[c] * re[c] + im[c] * im[c];
+        rho += m[c];
+        kin += dr[c] * dr[c] + di[c] * di[c];
+        lzi += re[c] * di[c] - im[c] * dr[c];       // Im(conj(phi) dphi)
+        acc[c] += m[c];
+      }
+      const double xr = co * x + si * y, yr = co * y - si * x;
+      acc[OB_WX] += xr * xr * rho;
+      acc[OB_WY] += yr * yr * rho;
+      acc[OB_WZ] += z * z * rho;
+      acc[OB_POT] += (a.gx2h * xr * xr + a.gy2h * yr * yr + a.gz2h * z * z) * rho;
+      const double Fz = 2.0 * (m[0] - m[4]) + m[1] - m[3];
+      // F_+ = 2(conj(p2)p1 + conj(m1)m2) + sqrt6 (conj(p1)p0 + conj(p0)m1)
+      const double fpr = 2.0 * (re[0] * re[1] + im[0] * im[1] + re[3] * re[4] + im[3] * im[4]) +
+                         s6 * (re[1] * re[2] + im[1] * im[2] + re[2] * re[3] + im[2] * im[3]);
+      const double fpi = 2.0 * (re[0] * im[1] - im[0] * re[1] + re[3] * im[4] - im[3] * re[4]) +
+                         s6 * (re[1] * im[2] - im[1] * re[2] + re[2] * im[3] - im[2] * re[3]);
+      const double aR = 2.0 * (re[0] * re[4] - im[0] * im[4]) - 2.0 * (re[1] * re[3] - im[1] * im[3]) +
+                        re[2] * re[2] - im[2] * im[2];
+      const double aI = 2.0 * (re[0] * im[4] + im[0] * re[4]) - 2.0 * (re[1] * im[3] + im[1] * re[3]) +
+                        2.0 * re[2] * im[2];
+      acc[OB_INT] += 0.5 * a.c0 * rho * rho + 0.5 * a.c1 * (fpr * fpr + fpi * fpi + Fz * Fz) +
+                     0.5 * a.c2 * (aR * aR + aI * aI) * 0.2;
+      acc[OB_KX] += 0.5 * kin;
+      acc[OB_LZX] += -y * lzi;
+      // SOC, x part: sum_i coef_i Re[-conj(phi_i) d phi_{i+1} + conj(phi_{i+1}) d phi_i]
+      const double coef[4] = {1.0, s6h, s6h, 1.0};
+      double soc = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double t1 = re[k] * dr[k + 1] + im[k] * di[k + 1];
+        const double t2 = re[k + 1] * dr[k] + im[k + 1] * di[k];
+        soc += coef[k] * (t2 - t1);
+      }
+      acc[OB_SOCX] += soc;
+    }
+  }
+  double* out = a.partials + ((size_t)blockIdx.y * a.nblocks + blockIdx.x) * OBX_NT;
+  block_sums<OBX_NT>(acc, out, red);
+}
+
+// strided lines: derivative terms along y (or z).
+template <typename R, int N, int E>
+__global__ void __launch_bounds__(LCfg<R, N, E>::THREADS)
+k_obs_line(ObsLArgs<R> a) {
+  typedef cplx<R> C;
+  typedef LCfg<R, N, E> Cfg;
+  constexpr int T = Cfg::T;
+  constexpr int TILE = Cfg::TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* xb = tw + N;
+  __shared__ double red[32 * 3];
+  const int col = threadIdx.x % TILE;
+  const int i = threadIdx.x / TILE;
+  for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
+  const int xcol = blockIdx.x * TILE + col;
+  const bool valid = xcol < a.nx;
+  const C* base = a.field + (size_t)blockIdx.z * 5 * a.ntot + (size_t)blockIdx.y * a.plane_stride +
+                  (valid ? xcol : 0) + (size_t)i * a.line_stride;
+  const size_t step = (size_t)T * a.line_stride;
+  C v[5][E];
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      v[c][e] = valid ? base[(size_t)c * a.ntot + e * step] : mkc((R)0, (R)0);
+  C* b0 = xb + col * Cfg::LP;
+  C* b1 = xb + (TILE + col) * Cfg::LP;
+  fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = i + T * e;
+    const int ps = p < N / 2 ? p : p - N;
+    const R f = (R)ps * a.dnu;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c][e] = cscale(cmuli(v[c][e]), f);
+  }
+  fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    const double x = a.x0 + xcol * a.hx;
+    const double s6h = 1.22474487139158904910;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      double re[5], im[5], dr[5], di[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const C u = base[(size_t)c * a.ntot + e * step];
+        re[c] = (double)u.x; im[c] = (double)u.y;
+        dr[c] = (double)v[c][e].x; di[c] = (double)v[c][e].y;
+      }
+      double kin = 0.0, lzi = 0.0;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        kin += dr[c] * dr[c] + di[c] * di[c];
+        lzi += re[c] * di[c] - im[c] * dr[c];
+      }
+      acc[0] += 0.5 * kin;
+      if (a.axis == 1) {
+        acc[1] += x * lzi;
+        // SOC, y part: sum_i coef_i Re[i conj(phi_i) d phi_{i+1} + i conj(phi_{i+1}) d phi_i]
+        const double coef[4] = {1.0, s6h, s6h, 1.0};
+        double soc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          // Re(i conj(a) b) = -(Im(conj(a) b)) = -(ar*bi - ai*br)
+          const double t1 = re[k] * di[k + 1] - im[k] * dr[k + 1];
+          const double t2 = re[k + 1] * di[k] - im[k + 1] * dr[k];
+          soc -= coef[k] * (t1 + t2);
+        }
+        acc[2] += soc;
+      }
+    }
+  }
+  double* out = a.partials +
+                ((size_t)blockIdx.z * a.nblocks + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * OBL_NT;
+  block_sums<OBL_NT>(acc, out, red);
+}
+
+// Fixed-order sum of per-block partials: out[m*ostride + ooff + k] =
+// sum_b part[(m*nblocks + b)*nterm + k].  One thread per (member, term).
+static __global__ void k_reduce_partials(const double* part, int nblocks, int nterm, int members,
+                                  double* out, int ostride, int ooff) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= members * nterm) return;
+  const int m = id / nterm, k = id - m * nterm;
+  const double* p = part + (size_t)m * nblocks * nterm + k;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += p[(size_t)b * nterm];
+  out[(size_t)m * ostride + ooff + k] = s;
+}
+
+}  // namespace sgp

@@ -1,0 +1,257 @@
+"""Thin Python binding of the C ABI in ``include/sgp.h`` (libsgp.so).
+
+Argument marshalling only: every step of the propagator runs in the CUDA
+library.  The functions keep the C names (create_grid, set_params,
+set_state, get_state, step, substep, observables, synchronize, destroy);
+``Context`` bundles them for convenience.  Fields are numpy arrays (host) or
+torch tensors (host or CUDA) of complex64 (F32 contexts) or complex128 (F64),
+shaped (batch, 5, [nz,] ny, nx) or, for batch 1, (5, [nz,] ny, nx).
+
+There is no fallback: if libsgp.so is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgp.so")
+
+SGP_F32, SGP_F64 = 32, 64
+SGP_TS2, SGP_TS4 = 0, 1
+SGP_SUB_NONLINEAR, SGP_SUB_LINEAR = 0, 1
+SCHEMES = {"ts2": SGP_TS2, "ts4": SGP_TS4}
+PRECS = {"f32": SGP_F32, "f64": SGP_F64}
+
+
+class SgpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status, msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("omega", "gamma", "c0", "c1", "c2", "gx", "gy", "gz")]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("mass", ctypes.c_double),
+                ("energy", ctypes.c_double), ("magnetization", ctypes.c_double),
+                ("lz", ctypes.c_double), ("comp_mass", ctypes.c_double * 5),
+                ("width2", ctypes.c_double * 3), ("e_kin", ctypes.c_double),
+                ("e_pot", ctypes.c_double), ("e_rot", ctypes.c_double),
+                ("e_int", ctypes.c_double), ("e_soc", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["comp_mass"] = list(self.comp_mass)
+        d["width2"] = list(self.width2)
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Load libsgp.so once (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsgp.so is not built (run __graft_entry__.build() or "
+                           "python paper_2603_25282_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "sgp_version": (I, []),
+        "sgp_status_string": (ctypes.c_char_p, [I]),
+        "sgp_last_error": (ctypes.c_char_p, [P]),
+        "sgp_create_grid": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                I, I, I, P, ctypes.POINTER(P)]),
+        "sgp_set_params": (I, [P, ctypes.POINTER(Params)]),
+        "sgp_set_state": (I, [P, P, I, D]),
+        "sgp_get_state": (I, [P, P, I]),
+        "sgp_get_time": (I, [P, ctypes.POINTER(ctypes.c_double)]),
+        "sgp_step": (I, [P, LL, D, I]),
+        "sgp_substep": (I, [P, I, D]),
+        "sgp_observables": (I, [P, ctypes.POINTER(Obs)]),
+        "sgp_synchronize": (I, [P]),
+        "sgp_launch_count": (LL, [P]),
+        "sgp_destroy": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        L = lib()
+        msg = L.sgp_last_error(ctx).decode()
+        raise SgpError(L.sgp_status_string(status).decode(), msg)
+
+
+def _ptr(x, dtype):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype:
+            raise TypeError("field dtype %s, expected %s" % (x.dtype, np.dtype(dtype)))
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("field must be C-contiguous")
+        return x.ctypes.data, 0, x
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        want = torch.complex64 if np.dtype(dtype) == np.complex64 else torch.complex128
+        if x.dtype != want:
+            raise TypeError("field dtype %s, expected %s" % (x.dtype, want))
+        if not x.is_contiguous():
+            raise ValueError("field must be contiguous")
+        return x.data_ptr(), int(x.is_cuda), x
+    raise TypeError("field must be a numpy array or a torch tensor")
+
+
+# ---------------------------------------------------------------------------
+# C-named functions
+# ---------------------------------------------------------------------------
+def create_grid(n, L, batch=1, prec="f32", device=0, stream=None):
+    """sgp_create_grid; n and L in (x, y[, z]) order.  Returns the handle."""
+    dim = len(n)
+    if np.isscalar(L):
+        L = [float(L)] * dim
+    m = max(3, dim)
+    na = (ctypes.c_int * m)(*(list(n) + [1] * (m - dim)))
+    La = (ctypes.c_double * m)(*(list(L) + [1.0] * (m - len(L))))
+    out = ctypes.c_void_p()
+    st = lib().sgp_create_grid(dim, na, La, int(batch), PRECS[prec] if isinstance(prec, str) else prec,
+                               int(device), ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    _check(st, None)
+    return out
+
+
+def set_params(ctx, **kw):
+    p = Params(**{k: float(kw.get(k, 1.0 if k in ("gx", "gy", "gz") else 0.0))
+                  for k, _ in Params._fields_})
+    _check(lib().sgp_set_params(ctx, ctypes.byref(p)), ctx)
+
+
+def set_state(ctx, src, dtype, t0=0.0):
+    ptr, dev, _keep = _ptr(src, dtype)
+    _check(lib().sgp_set_state(ctx, ctypes.c_void_p(ptr), dev, float(t0)), ctx)
+
+
+def get_state(ctx, dst, dtype):
+    ptr, dev, _keep = _ptr(dst, dtype)
+    _check(lib().sgp_get_state(ctx, ctypes.c_void_p(ptr), dev), ctx)
+    return dst
+
+
+def get_time(ctx):
+    t = ctypes.c_double()
+    _check(lib().sgp_get_time(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def step(ctx, nsteps, dt, scheme="ts2"):
+    s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+    _check(lib().sgp_step(ctx, int(nsteps), float(dt), s), ctx)
+
+
+def substep(ctx, kind, delta):
+    k = {"nonlinear": SGP_SUB_NONLINEAR, "linear": SGP_SUB_LINEAR}.get(kind, kind)
+    _check(lib().sgp_substep(ctx, k, float(delta)), ctx)
+
+
+def observables(ctx, batch=1):
+    arr = (Obs * batch)()
+    _check(lib().sgp_observables(ctx, arr), ctx)
+    return [o.as_dict() for o in arr]
+
+
+def synchronize(ctx):
+    _check(lib().sgp_synchronize(ctx), ctx)
+
+
+def launch_count(ctx):
+    return int(lib().sgp_launch_count(ctx))
+
+
+def destroy(ctx):
+    if ctx:
+        _check(lib().sgp_destroy(ctx), None)
+
+
+# ---------------------------------------------------------------------------
+# convenience object
+# ---------------------------------------------------------------------------
+class Context:
+    """One sgp context: grid, precision, batch, device and stream."""
+
+    def __init__(self, n, L, batch=1, prec="f32", device=0, stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.L = (float(L),) * len(n) if np.isscalar(L) else tuple(float(v) for v in L)
+        self.batch = int(batch)
+        self.prec = prec
+        self.dtype = np.complex64 if prec == "f32" else np.complex128
+        self.handle = create_grid(self.n, self.L, batch, prec, device, stream)
+
+    @property
+    def shape(self):
+        return (self.batch, 5) + self.n[::-1]
+
+    def set_params(self, **kw):
+        set_params(self.handle, **kw)
+
+    def set_state(self, src, t0=0.0):
+        set_state(self.handle, src, self.dtype, t0)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        get_state(self.handle, out, self.dtype)
+        return out
+
+    @property
+    def t(self):
+        return get_time(self.handle)
+
+    def step(self, nsteps, dt, scheme="ts2"):
+        step(self.handle, nsteps, dt, scheme)
+
+    def substep(self, kind, delta):
+        substep(self.handle, kind, delta)
+
+    def observables(self):
+        return observables(self.handle, self.batch)
+
+    def synchronize(self):
+        synchronize(self.handle)
+
+    def launch_count(self):
+        return launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every symbol include/sgp.h declares
+(no GPU needed: only argument validation that returns before any CUDA work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2603_25282_gb300 import sgp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "sgp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgp_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(sgp.LIB_PATH):
+        from paper_2603_25282_gb300 import build
+        build.build()
+    return sgp.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings(lib):
+    assert lib.sgp_version() >= 100
+    assert lib.sgp_status_string(0) == b"SGP_OK"
+    assert lib.sgp_status_string(1) == b"SGP_EINVAL"
+
+
+def test_create_grid_rejects_bad_arguments_before_cuda(lib):
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        sgp.create_grid((64, 64, 64, 64), 8.0)        # dim 4
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        sgp.create_grid((100, 64), 8.0)               # unsupported N
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        sgp.create_grid((64, 64), -1.0)               # L <= 0
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        sgp.create_grid((64, 64), 8.0, batch=0)
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        sgp.create_grid((64, 64), 8.0, prec=16)
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.sgp_step(None, 1, 0.1, 0) == 1
+    assert lib.sgp_observables(None, None) == 1
+    assert lib.sgp_destroy(None) == 0
