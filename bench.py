@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Throughput of the compact splitting propagator on GB300.
+
+Workload (default): the 2D spin-2 system on a 512x512 grid over [-16,16]^2,
+Omega = 0.9, gamma = 1.5, c = (1000, -5, 10), isotropic unit trap, TS4,
+dt = 5e-4, FP32 fields (FP64 time, angles, tables, reductions), seeded
+Gaussian + 0.01 random-phase initial data.  A batch of B independent seeded
+members makes the resident field (B x 10.5 MB) larger than the 129 MB L2, so
+every pass streams from HBM.  One bench step = one TS4 time step of every
+member (3 line passes + 3 x-passes in the merged steady state).
+
+Metric: 5-component grid-point-steps per second (whole job), plus the HBM
+roofline of the dominant kernel from CUDA events recorded around every
+launch, the FP64 oracle timed on the host cores (cpu_baseline) and an
+end-to-end number through the C ABI with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (n, L, params, scheme, dt, prec, batch)
+    "2d512_ts4_f32": ((512, 512), 16.0,
+                      dict(omega=0.9, gamma=1.5, c0=1000.0, c1=-5.0, c2=10.0, gx=1.0, gy=1.0, gz=1.0),
+                      "ts4", 5e-4, "f32", 32),
+    "2d512_ts4_f64": ((512, 512), 16.0,
+                      dict(omega=0.9, gamma=1.5, c0=1000.0, c1=-5.0, c2=10.0, gx=1.0, gy=1.0, gz=1.0),
+                      "ts4", 5e-4, "f64", 16),
+    "3d128_ts2_f32": ((128, 128, 128), 8.0,
+                      dict(omega=0.7, gamma=1.0, c0=500.0, c1=-2.0, c2=5.0, gx=1.0, gy=1.0, gz=2.0),
+                      "ts2", 1e-3, "f32", 4),
+    "3d128_ts4_f32": ((128, 128, 128), 8.0,
+                      dict(omega=0.7, gamma=1.0, c0=500.0, c1=-2.0, c2=5.0, gx=1.0, gy=1.0, gz=2.0),
+                      "ts4", 1e-3, "f32", 4),
+}
+METRIC = "5-comp grid-pt*steps/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def bytes_per_point_step(dim, scheme, prec):
+    """Algorithmic HBM bytes per grid-point-step: each pass reads and writes
+    the five-component field once (s = 40 B FP32, 80 B FP64); the merged
+    steady state has 2 passes per (L, N) pair in 2D and 4 in 3D; TS2 has one
+    pair per step, TS4 three."""
+    s = 40 if prec == "f32" else 80
+    pairs = 1 if scheme == "ts2" else 3
+    passes = 2 if dim == 2 else 4
+    return 2 * s * passes * pairs, 2 * s
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling (nvidia-smi, during the timed region)
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, single-threaded subprocess
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+from oracle import sgp_oracle as O
+from paper_2603_25282_gb300 import inputs
+n, L, prm, scheme, dt, steps, warmup, budget = %(args)s
+g = O.Grid(tuple(n), L)
+pr = O.Propagator(g, O.Params(**prm))
+psi = inputs.gaussian_random_phase(tuple(n), L, seed=2, amp=0.01)
+t = 0.0
+psi, t = pr.run(psi, t, dt, max(1, warmup), scheme)   # also builds the mode matrices
+done = 0
+t0 = time.perf_counter()
+while done < steps:
+    psi, t = pr.step(psi, t, dt, scheme)
+    done += 1
+    if time.perf_counter() - t0 > budget:
+        break
+dtm = time.perf_counter() - t0
+print(json.dumps({"seconds": dtm, "steps": done}))
+"""
+
+
+def run_oracle_sample(wl, steps, warmup=1, budget=20.0):
+    """Time the oracle on one member of the workload: `warmup` untimed steps,
+    then up to `steps` timed steps or until `budget` seconds have passed."""
+    n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = ORACLE_SNIPPET % {"root": ROOT, "args": repr((list(n), L, prm, scheme, dt, steps,
+                                                          warmup, budget))}
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    pts = math.prod(n)
+    return pts * d["steps"] / d["seconds"], d
+
+
+def cpu_baseline_block(wl, steps):
+    v, d = run_oracle_sample(wl, steps)
+    n = WORKLOADS[wl][0]
+    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "%d %s steps of one %s member (FP64 numpy oracle, 1 thread, %.1f s)"
+                      % (d["steps"], WORKLOADS[wl][3].upper(), "x".join(map(str, n)), d["seconds"])}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl = args.workload
+    n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
+    # W untimed steps, then up to K timed steps within a bounded wall time
+    v, d = run_oracle_sample(wl, max(1, args.steps), args.warmup, budget=90.0)
+    line = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * d["seconds"] / d["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl, "grid": list(n), "scheme": scheme, "dt": dt,
+                       "members_timed": 1},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": "%d timed %s steps (after %d warm-up) of one member, FP64 "
+                                       "numpy oracle, 1 thread, %.1f s"
+                                       % (d["steps"], scheme.upper(), args.warmup, d["seconds"])},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2603_25282_gb300 import inputs, sgp
+    from paper_2603_25282_gb300 import build as _build
+
+    _build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    wl = args.workload
+    n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
+    if args.batch:
+        batch = args.batch
+    dim = len(n)
+    ctx = sgp.Context(n, L, batch=batch, prec=prec, device=local_rank, stream=stream.cuda_stream)
+    ctx.set_params(**prm)
+    cdt = np.complex64 if prec == "f32" else np.complex128
+    tdt = torch.complex64 if prec == "f32" else torch.complex128
+    host = np.stack([inputs.gaussian_random_phase(n, L, seed=1000 * rank + m + 2, amp=0.01)
+                     for m in range(batch)]).astype(cdt)
+    dev_init = torch.from_numpy(host).to(f"cuda:{local_rank}")
+    pts = math.prod(n)
+    state_bytes = host.nbytes
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local_rank}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-resident timing -------------------------------------------
+    ctx.set_state(dev_init, 0.0)
+    ctx.step(args.warmup, dt, scheme)
+    barrier()
+    l0 = ctx.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        ctx.step(args.steps, dt, scheme)
+        ev1.record(stream)
+        barrier()
+    launches = ctx.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms)
+    clocks = clk.summary()
+    value = world * batch * pts * args.steps / (ms * 1e-3)
+
+    # ---- per-kernel roofline (CUDA events around every launch) ------------
+    ctx.set_profiling(True)
+    ctx.step(args.steps, dt, scheme)
+    prof = ctx.get_profile()
+    ctx.set_profiling(False)
+    hbm_peak, peak_src = peaks()
+    per_pass_bytes = 2 * state_bytes          # one read + one write of the field
+    kinds = {k: v for k, v in prof.items() if k in ("xpass", "linepass_y", "linepass_z") and v[0]}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    dom_avg_ms = kinds[dom][1] / kinds[dom][0]
+    achieved = per_pass_bytes / (dom_avg_ms * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tr_path) as f:
+            tr = json.load(f)
+        key = "%s:%s" % (wl, dom)
+        if key in tr:
+            traffic = tr[key]
+    except Exception:
+        pass
+    bpp, bmin = bytes_per_point_step(dim, scheme, prec)
+    step_gbs = bpp * pts * batch * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    pinned = torch.from_numpy(host).pin_memory()
+    out_pinned = torch.empty_like(pinned).pin_memory()
+    e2e_steps = max(1, min(args.steps, 8))
+    ctx.set_state(pinned, 0.0)
+    ctx.step(1, dt, scheme)
+    ctx.get_state(out_pinned)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(pinned, 0.0)
+        ctx.step(1, dt, scheme)
+        ctx.get_state(out_pinned)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * batch * pts * e2e_steps / e2e_s
+
+    # ---- CPU baseline (rank 0, N = 1) --------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline_block(wl, args.cpu_steps)
+        except Exception as e:  # the GPU number stands without it
+            cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "sample": "failed: %s" % str(e)[:200]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": prec, "data": "synthetic",
+            "config": {"workload": wl, "grid": list(n), "L": L, "scheme": scheme, "dt": dt,
+                       "members_per_gpu": batch, "params": prm,
+                       "field_bytes_per_gpu": state_bytes,
+                       "l2": "field %.0f MB > L2 %.0f MB (inputs larger than L2)"
+                             % (state_bytes / 1e6, L2_BYTES / 1e6),
+                       "parallelism": "replicas%d" % world},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": traffic, "bytes_per_launch": per_pass_bytes,
+                         "avg_launch_ms": dom_avg_ms,
+                         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}},
+            "step_hbm": {"algorithmic_bytes_per_point_step": bpp, "achieved_gbs": step_gbs,
+                         "frac": step_gbs / hbm_peak,
+                         "compulsory_bytes_per_point_step": bmin},
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes, "steps": e2e_steps,
+                    "note": "per step: set_state from pinned host, one step, get_state to pinned host"},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d512_ts4_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -161,6 +161,15 @@ sgp_status sgp_synchronize(sgp_ctx* ctx);
 /* Number of kernels this context has launched so far (for accounting). */
 long long sgp_launch_count(const sgp_ctx* ctx);
 
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * every launch while enabled (adds one event pair per launch).  Kinds:
+ * 0 x-pass, 1 line pass along y, 2 line pass along z, 3 tables,
+ * 4 observables, 5 other.  sgp_get_profile synchronises, writes the number
+ * of launches and the summed device milliseconds of each kind into
+ * launches[0..5] and ms[0..5], and clears the record.  Enabling clears too. */
+sgp_status sgp_set_profiling(sgp_ctx* ctx, int enable);
+sgp_status sgp_get_profile(sgp_ctx* ctx, long long* launches, double* ms);
+
 /* Free the context and its device memory (synchronises first).  NULL is a
  * no-op. */
 sgp_status sgp_destroy(sgp_ctx* ctx);

@@ -28,6 +28,39 @@ const double kB2 = -kCbrt2 / (2.0 - kCbrt2);
 // ----------------------------------------------------------------------------
 // table kernels (FP64 arithmetic, stored in the context precision)
 // ----------------------------------------------------------------------------
+// Rounding of an FP64 complex target to the working precision.  For FP32
+// the 5x5 neighbourhood (+-2 ulp per coordinate) of the rounded pair is
+// searched for the smallest |z - target| + ||z| - |target||: the factors are
+// applied in every step, so a modulus error of the stored value would turn
+// into a steady drift of the mass.
+__device__ inline void store_pair(double tx, double ty, float* ox, float* oy) {
+  const double m = sqrt(tx * tx + ty * ty);
+  float xs[5], ys[5];
+  xs[2] = (float)tx;
+  ys[2] = (float)ty;
+  xs[1] = nextafterf(xs[2], -INFINITY); xs[0] = nextafterf(xs[1], -INFINITY);
+  xs[3] = nextafterf(xs[2], INFINITY);  xs[4] = nextafterf(xs[3], INFINITY);
+  ys[1] = nextafterf(ys[2], -INFINITY); ys[0] = nextafterf(ys[1], -INFINITY);
+  ys[3] = nextafterf(ys[2], INFINITY);  ys[4] = nextafterf(ys[3], INFINITY);
+  double best = 1e300;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) {
+      const double x = xs[a], y = ys[b];
+      const double dz = sqrt((x - tx) * (x - tx) + (y - ty) * (y - ty));
+      const double dm = fabs(sqrt(x * x + y * y) - m);
+      const double sc = dz + dm;
+      if (sc < best) {
+        best = sc;
+        *ox = xs[a];
+        *oy = ys[b];
+      }
+    }
+}
+__device__ inline void store_pair(double tx, double ty, double* ox, double* oy) {
+  *ox = tx;
+  *oy = ty;
+}
+
 // W_N^k = exp(-2 pi i k / N), k < N.
 template <typename R>
 __global__ void k_twiddles(int N, cplx<R>* out) {
@@ -35,55 +68,58 @@ __global__ void k_twiddles(int N, cplx<R>* out) {
   if (k >= N) return;
   double s, c;
   sincospi(-2.0 * (double)k / (double)N, &s, &c);
-  out[k] = mkc((R)c, (R)s);
+  R x, y;
+  store_pair(c, s, &x, &y);
+  out[k] = mkc(x, y);
 }
 
-// Per-substep tables of the linear flow over delta (Sec. 3.1, Eq. (sl1)):
-//  lam[(|p|, |q|)] = (ahat, cp, sp) of U = exp(i delta lambda n.sigma/2),
-//    lambda = sqrt(Omega^2 + gamma^2 |nu_perp|^2),
-//    U11 = cos(th/2) - i sin(th/2) Omega/lambda = cp * ahat,
-//    U12 = sin(th/2) gamma (nu_x - i nu_y)/lambda = sp * (nu_x - i nu_y)/|nu_perp|;
-//  kin_a[p] = exp(-i nu_p^2 delta/2) / N_a for each axis a (the 1/N of the
-//    forward transforms is folded in here).
+// Per-mode table of the linear flow over delta (Sec. 3.1, Eq. (sl1)), one
+// entry per (|p|, |q|) in the layout MT_* of sgp_kernels.cuh; the angles are
+// formed and the exponentials evaluated in FP64.  kz[r] = exp(-i nu_z^2 d/2)/NZ.
 template <typename R>
 __global__ void k_linear_tables(double delta, double omega, double gamma, int NX, int NY,
-                                int NZ, double Lx, double Ly, double Lz, R* lam,
-                                cplx<R>* kx, cplx<R>* ky, cplx<R>* kz) {
+                                int NZ, double Lx, double Ly, double Lz, R* mt, cplx<R>* kz) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int hq = NY / 2 + 1;
-  const int nlam = (NX / 2 + 1) * hq;
-  if (id < nlam) {
+  const int nent = (NX / 2 + 1) * hq;
+  if (id < nent) {
     const int ap = id / hq, aq = id - ap * hq;
     const double nup = kPi * ap / Lx, nuq = kPi * aq / Ly;
     const double nperp = sqrt(nup * nup + nuq * nuq);
     const double lamb = sqrt(omega * omega + gamma * gamma * nperp * nperp);
     double ar = 1.0, ai = 0.0, cp = 1.0, sp = 0.0;
     if (lamb > 0.0) {
-      double s, c;
-      sincos(0.5 * delta * lamb, &s, &c);
-      const double ur = c, ui = -s * omega / lamb;
+      double sn, cs;
+      sincos(0.5 * delta * lamb, &sn, &cs);
+      const double ur = cs, ui = -sn * omega / lamb;
       cp = sqrt(ur * ur + ui * ui);
       if (cp > 0.0) {
         ar = ur / cp;
         ai = ui / cp;
       }
-      sp = s * gamma * nperp / lamb;
+      sp = sn * gamma * nperp / lamb;
     }
-    lam[4 * id + 0] = (R)ar;
-    lam[4 * id + 1] = (R)ai;
-    lam[4 * id + 2] = (R)cp;
-    lam[4 * id + 3] = (R)sp;
+    double ks, kc;
+    sincos(-0.5 * (nup * nup + nuq * nuq) * delta, &ks, &kc);
+    const double inv = 1.0 / ((double)NX * (double)NY);
+    R* e = mt + (size_t)MT_STRIDE * id;
+    store_pair(kc * inv, ks * inv, &e[MT_KR], &e[MT_KI]);
+    store_pair(ar, ai, &e[MT_AR], &e[MT_AI]);
+    store_pair(cp, sp, &e[MT_CP], &e[MT_SP]);
+    if (nperp > 0.0)
+      store_pair(nup / nperp, nuq / nperp, &e[MT_BX], &e[MT_BY]);
+    else
+      store_pair(1.0, 0.0, &e[MT_BX], &e[MT_BY]);
   }
-  auto kin = [&](int k, int N, double L, cplx<R>* out) {
-    const int ks = k < N / 2 ? k : k - N;
-    const double nu = kPi * ks / L;
-    double s, c;
-    sincos(-0.5 * nu * nu * delta, &s, &c);
-    out[k] = mkc((R)(c / N), (R)(s / N));
-  };
-  if (id < NX) kin(id, NX, Lx, kx);
-  if (id < NY) kin(id, NY, Ly, ky);
-  if (id < NZ) kin(id, NZ, Lz, kz);
+  if (id < NZ) {
+    const int ks_ = id < NZ / 2 ? id : id - NZ;
+    const double nu = kPi * ks_ / Lz;
+    double sn, cs;
+    sincos(-0.5 * nu * nu * delta, &sn, &cs);
+    R x, y;
+    store_pair(cs / NZ, sn / NZ, &x, &y);
+    kz[id] = mkc(x, y);
+  }
 }
 
 __global__ void k_set_time(double* t, double v) { *t = v; }
@@ -93,8 +129,8 @@ __global__ void k_set_time(double* t, double v) { *t = v; }
 // ----------------------------------------------------------------------------
 struct LinTables {
   double delta = 0.0;
-  void* lam = nullptr;
-  void* kin[3] = {nullptr, nullptr, nullptr};
+  void* mt = nullptr;    // per-mode table, MT_STRIDE values per (|p|, |q|)
+  void* kz = nullptr;    // z kinetic factors (NZ entries)
 };
 
 }  // namespace
@@ -122,6 +158,10 @@ struct sgp_ctx {
   size_t partials_len = 0;
   double* obs_dev = nullptr;        // [batch][OB_NT]
   long long launches = 0;
+  // profiling: event pairs per launch kind (enabled by sgp_set_profiling)
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+  std::vector<cudaEvent_t> event_pool;
   std::string err;
 };
 
@@ -150,6 +190,39 @@ sgp_status fail(sgp_ctx* c, sgp_status s, const char* fmt, ...) {
                   __FILE__, __LINE__);                                                   \
   } while (0)
 
+enum { PK_X = 0, PK_Y = 1, PK_Z = 2, PK_TAB = 3, PK_OBS = 4, PK_OTHER = 5, PK_N = 6 };
+
+cudaEvent_t take_event(sgp_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around one launch when profiling is on.
+struct ProfScope {
+  sgp_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(sgp_ctx* ctx, int k) : c(ctx), kind(k) {
+    if (c->profiling) {
+      a = take_event(c);
+      b = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEventRecord(b, c->stream);
+      c->prof.push_back({kind, {a, b}});
+    }
+  }
+};
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -171,8 +244,8 @@ bool finite_params(const sgp_params* p) {
 
 void free_tables(sgp_ctx* c) {
   for (auto& t : c->tables) {
-    cudaFree(t.lam);
-    for (void* k : t.kin) cudaFree(k);
+    cudaFree(t.mt);
+    cudaFree(t.kz);
   }
   c->tables.clear();
 }
@@ -188,13 +261,14 @@ sgp_status get_tables(sgp_ctx* c, double delta, const LinTables** out) {
   LinTables t;
   t.delta = delta;
   const int NX = c->n[0], NY = c->n[1], NZ = c->n[2];
-  const size_t nlam = (size_t)(NX / 2 + 1) * (NY / 2 + 1);
-  SGP_CUDA(c, cudaMalloc(&t.lam, nlam * 4 * sizeof(R)));
-  for (int a = 0; a < 3; ++a) SGP_CUDA(c, cudaMalloc(&t.kin[a], (size_t)c->n[a] * sizeof(cplx<R>)));
-  const int work = (int)std::max<size_t>(nlam, (size_t)std::max(NX, std::max(NY, NZ)));
+  const size_t nent = (size_t)(NX / 2 + 1) * (NY / 2 + 1);
+  SGP_CUDA(c, cudaMalloc(&t.mt, nent * MT_STRIDE * sizeof(R)));
+  SGP_CUDA(c, cudaMalloc(&t.kz, (size_t)NZ * sizeof(cplx<R>)));
+  const int work = (int)std::max<size_t>(nent, (size_t)NZ);
+  ProfScope ps(c, PK_TAB);
   k_linear_tables<R><<<(work + 255) / 256, 256, 0, c->stream>>>(
-      delta, c->prm.omega, c->prm.gamma, NX, NY, NZ, c->L[0], c->L[1], c->L[2], (R*)t.lam,
-      (cplx<R>*)t.kin[0], (cplx<R>*)t.kin[1], (cplx<R>*)t.kin[2]);
+      delta, c->prm.omega, c->prm.gamma, NX, NY, NZ, c->L[0], c->L[1], c->L[2], (R*)t.mt,
+      (cplx<R>*)t.kz);
   c->launches++;
   SGP_CUDA(c, cudaGetLastError());
   c->tables.push_back(t);
@@ -231,6 +305,7 @@ sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
   a.t_base = c->t_dev;
   a.t_off = t_off;
   c->launches++;
+  ProfScope ps(c, PK_X);
   SGP_CUDA(c, launch_xpass<R>(c->n[0], a, c->batch, c->stream));
   return SGP_OK;
 }
@@ -259,14 +334,11 @@ sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
   a.NX = c->n[0];
   a.NY = c->n[1];
   if (t) {
-    a.lam = (const R*)t->lam;
-    a.kx = (const cplx<R>*)t->kin[0];
-    a.ky = (const cplx<R>*)t->kin[1];
-    a.kz = (const cplx<R>*)t->kin[2];
+    a.mt = (const R*)t->mt;
+    a.kz = (const cplx<R>*)t->kz;
   }
-  a.pix = (R)(kPi / c->L[0]);
-  a.piy = (R)(kPi / c->L[1]);
   c->launches++;
+  ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
   SGP_CUDA(c, launch_linepass<R>(c->n[axis], a, planes, c->batch, c->stream));
   return SGP_OK;
 }
@@ -308,7 +380,10 @@ sgp_status run_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   }
   const double t0 = c->t;
   c->launches++;
-  k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, t0);
+  {
+    ProfScope ps(c, PK_OTHER);
+    k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, t0);
+  }
   SGP_CUDA(c, cudaGetLastError());
   // first nonlinear substep (physical in, x-spectral out)
   SGP_TRY(x_pass<R>(c, XP_NL | XP_FWD, seq[0].second * dt, 0.0));
@@ -386,7 +461,10 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
   ax.dnu = (R)(kPi / c->L[0] / NX);
   ax.NX = NX;
   c->launches++;
-  SGP_CUDA(c, launch_obs_x<R>(NX, ax, c->batch, c->stream));
+  {
+    ProfScope ps(c, PK_OBS);
+    SGP_CUDA(c, launch_obs_x<R>(NX, ax, c->batch, c->stream));
+  }
   c->launches++;
   k_reduce_partials<<<(c->batch * OBX_NT + 127) / 128, 128, 0, c->stream>>>(
       c->partials, nbx, OBX_NT, c->batch, c->obs_dev, OB_NT, 0);
@@ -416,7 +494,10 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
     const int tiles = (NX + gl.rows_or_tile - 1) / gl.rows_or_tile;
     al.nblocks = tiles * planes;
     c->launches++;
-    SGP_CUDA(c, launch_obs_line<R>(NL, al, planes, c->batch, c->stream));
+    {
+      ProfScope ps(c, PK_OBS);
+      SGP_CUDA(c, launch_obs_line<R>(NL, al, planes, c->batch, c->stream));
+    }
     c->launches++;
     k_reduce_partials<<<(c->batch * OBL_NT + 127) / 128, 128, 0, c->stream>>>(
         c->partials, al.nblocks, OBL_NT, c->batch, c->obs_dev, OB_NT,
@@ -655,6 +736,41 @@ sgp_status sgp_synchronize(sgp_ctx* c) {
 
 long long sgp_launch_count(const sgp_ctx* c) { return c ? c->launches : 0; }
 
+static void recycle_events(sgp_ctx* c) {
+  for (auto& p : c->prof) {
+    c->event_pool.push_back(p.second.first);
+    c->event_pool.push_back(p.second.second);
+  }
+  c->prof.clear();
+}
+
+sgp_status sgp_set_profiling(sgp_ctx* c, int enable) {
+  if (!c) return SGP_EINVAL;
+  DeviceGuard guard(c->device);
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  recycle_events(c);
+  c->profiling = enable != 0;
+  return SGP_OK;
+}
+
+sgp_status sgp_get_profile(sgp_ctx* c, long long* launches, double* ms) {
+  if (!c || !launches || !ms) return SGP_EINVAL;
+  DeviceGuard guard(c->device);
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < PK_N; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  for (auto& p : c->prof) {
+    float t = 0.f;
+    SGP_CUDA(c, cudaEventElapsedTime(&t, p.second.first, p.second.second));
+    launches[p.first] += 1;
+    ms[p.first] += t;
+  }
+  recycle_events(c);
+  return SGP_OK;
+}
+
 sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;
   DeviceGuard guard(c->device);
@@ -665,6 +781,8 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   cudaFree(c->t_dev);
   cudaFree(c->partials);
   cudaFree(c->obs_dev);
+  recycle_events(c);
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   delete c;
   return SGP_OK;
 }

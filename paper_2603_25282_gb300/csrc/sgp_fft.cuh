@@ -281,6 +281,72 @@ struct FftStages {
   }
 };
 
+// Exact adjoint of FftStages<..., -1, ...>: the stages in reverse order, each
+// gathering its butterfly inputs from the forward stage's scatter positions,
+// applying the inverse RD-point DFT and then the conjugated twiddles, and
+// leaving its outputs at the forward stage's input positions (layout A).
+// With the same rounded twiddle table, forward followed by this adjoint
+// equals N times the identity up to |W|^2 - 1 and butterfly rounding: the
+// twiddle phase errors cancel instead of accumulating over many steps.
+template <typename R, int N, int E, int NC, int S, int NS>
+struct FftStagesAdj {
+  typedef cplx<R> C;
+  __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const C* tw,
+                                             C* b0, C* b1) {
+    constexpr int RD = radix_at(N, E, S);
+    if constexpr (RD > 0) {
+      // later forward stages come first in the adjoint
+      FftStagesAdj<R, N, E, NC, S + 1, NS * RD>::run(v, i, tw, b0, b1);
+      constexpr int T = N / E;
+      constexpr int B = E / RD;
+      constexpr bool LAST = (NS * RD == N);
+      constexpr int TSTEP = N / (NS * RD);
+      C w[B][RD];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        w[k][0] = mkc((R)1, (R)0);
+        if constexpr (NS > 1) {
+          const int j = (i + T * k) % NS;
+#pragma unroll
+          for (int r = 1; r < RD; ++r) w[k][r] = cconj(tw[j * r * TSTEP]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        C* buf = ((S * NC + c) & 1) ? b1 : b0;
+        if constexpr (!LAST) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) buf[padx<R>(i + T * e)] = v[c][e];
+          __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          C x[RD];
+          if constexpr (LAST) {
+#pragma unroll
+            for (int r = 0; r < RD; ++r) x[r] = v[c][k + r * B];
+          } else {
+            const int b = i + T * k;
+            const int idxD = (b / NS) * NS * RD + (b % NS);
+#pragma unroll
+            for (int r = 0; r < RD; ++r) x[r] = buf[padx<R>(idxD + r * NS)];
+          }
+          Dft<RD, +1, C>::run(x);
+#pragma unroll
+          for (int r = 0; r < RD; ++r) {
+            if constexpr (NS > 1) {
+              if (r > 0) x[r] = cmul(x[r], w[k][r]);
+            }
+            v[c][k + r * B] = x[r];
+          }
+        }
+      }
+    }
+  }
+};
+
+// Forward (DIR = -1) or inverse (DIR = +1, the exact adjoint of the forward,
+// unnormalised) transform of NC lines held in layout A.
 template <typename R, int N, int E, int DIR, int NC>
 __device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i,
                                           const cplx<R>* tw, cplx<R>* b0,
@@ -288,7 +354,10 @@ __device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i,
   static_assert(plan_ok(N, E), "no radix plan for this (N, E)");
   // the previous user of the exchange buffers may still be reading
   __syncthreads();
-  FftStages<R, N, E, DIR, NC, 0, 1>::run(v, i, tw, b0, b1);
+  if constexpr (DIR < 0)
+    FftStages<R, N, E, -1, NC, 0, 1>::run(v, i, tw, b0, b1);
+  else
+    FftStagesAdj<R, N, E, NC, 0, 1>::run(v, i, tw, b0, b1);
 }
 
 }  // namespace sgp

@@ -56,12 +56,19 @@ struct LPassArgs {
   int mode;
   int axis;                   // 1: lines along y (2D); 2: lines along z (3D)
   int NX, NY;                 // grid sizes along x and y (mode indices)
-  const R* lam;               // [(NX/2+1)*(NY/2+1)][4]: ahat.re, ahat.im, cp, sp
-  const cplx<R>* kx;          // exp(-i nu_x^2 d/2)/NX etc.
-  const cplx<R>* ky;
-  const cplx<R>* kz;
-  R pix, piy;                 // pi/Lx, pi/Ly
+  // per-mode table over (|p|, |q|), MT_STRIDE values per entry (see MT_*)
+  const R* mt;
+  const cplx<R>* kz;          // exp(-i nu_z^2 d/2)/NZ (3D only)
 };
+
+// Entry layout of the per-mode table of the linear flow over delta, indexed
+// by (|p|, |q|) (everything below depends on nu_x^2 and nu_y^2 only):
+//   K     = exp(-i (nu_x^2 + nu_y^2) delta/2) / (NX NY)
+//   ahat  = U11/|U11|, cp = |U11|, sp = signed |U12| of
+//           U = exp(i delta lambda n.sigma/2), lambda^2 = Omega^2 + gamma^2 |nu_perp|^2
+//   (bx, by) = (|nu_x|, |nu_y|)/|nu_perp|; the mode direction is
+//           bhat = (sign(p) bx, -sign(q) by) = (nu_x - i nu_y)/|nu_perp|.
+enum { MT_KR = 0, MT_KI, MT_AR, MT_AI, MT_CP, MT_SP, MT_BX, MT_BY, MT_STRIDE };
 
 // ----------------------------------------------------------------------------
 // spin-2 image of an SU(2) element in the factorised form
@@ -132,7 +139,14 @@ __device__ __forceinline__ void apply_spin2(cplx<R> (&v)[5], cplx<R> ahat,
 
 __device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sincos(a, s, c); }
-__device__ __forceinline__ float rsqrt_r(float a) { return rsqrtf(a); }
+// 1/sqrt(a): the hardware estimate plus one Newton step (about 0.5 ulp and
+// without the estimate's bias, which would otherwise make the spin-2
+// rotation below systematically non-unitary in FP32).
+__device__ __forceinline__ float rsqrt_r(float a) {
+  const float r = rsqrtf(a);
+  const float e = fmaf(-a * r, r, 1.0f);
+  return fmaf(0.5f * r, e, r);
+}
 __device__ __forceinline__ double rsqrt_r(double a) { return rsqrt(a); }
 
 // unit complex in the direction of u (1 if u == 0) and |u|
@@ -205,6 +219,12 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   R cp, sp;
   const C ahat = unit_dir(U11, cp);
   const C bhat = unit_dir(U12, sp);
+  {
+    // cp^2 + sp^2 = 1 to rounding (d(cp, sp) is homogeneous of degree 4)
+    const R nrm = rsqrt_r(fma(cp, cp, sp * sp));
+    cp *= nrm;
+    sp *= nrm;
+  }
   // scalar phase exp(-i d (V + (c0 + c2/5) rho))
   R ps, pc;
   sincos_r(-delta * (V + c0p * rho), &ps, &pc);
@@ -300,20 +320,17 @@ struct LCfg {
   static constexpr size_t SMEM = sizeof(cplx<R>) * (size_t)(N + 2 * TILE * LP);
 };
 
-template <typename R>
-__device__ __forceinline__ void load_lam(const R* lam, int idx, R& ar, R& ai, R& cp, R& sp);
-template <>
-__device__ __forceinline__ void load_lam<float>(const float* lam, int idx, float& ar,
-                                                float& ai, float& cp, float& sp) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(lam) + idx);
-  ar = t.x; ai = t.y; cp = t.z; sp = t.w;
+template <typename R> struct ModeEntry { R kr, ki, ar, ai, cp, sp, bx, by; };
+
+__device__ __forceinline__ ModeEntry<float> load_mode(const float* mt, int idx) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(mt) + 2 * idx);
+  const float4 b = __ldg(reinterpret_cast<const float4*>(mt) + 2 * idx + 1);
+  return ModeEntry<float>{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 }
-template <>
-__device__ __forceinline__ void load_lam<double>(const double* lam, int idx, double& ar,
-                                                 double& ai, double& cp, double& sp) {
-  const double2 t0 = __ldg(reinterpret_cast<const double2*>(lam) + 2 * idx);
-  const double2 t1 = __ldg(reinterpret_cast<const double2*>(lam) + 2 * idx + 1);
-  ar = t0.x; ai = t0.y; cp = t1.x; sp = t1.y;
+__device__ __forceinline__ ModeEntry<double> load_mode(const double* mt, int idx) {
+  const double2* q = reinterpret_cast<const double2*>(mt) + 4 * idx;
+  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  return ModeEntry<double>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
 }
 
 // linear flow of one Fourier mode (p, q, r in FFT order)
@@ -325,14 +342,11 @@ __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
   const int qs = q < a.NY / 2 ? q : q - a.NY;
   const int aps = ps < 0 ? -ps : ps;
   const int aqs = qs < 0 ? -qs : qs;
-  R ar, ai, cp, sp;
-  load_lam<R>(a.lam, aps * (a.NY / 2 + 1) + aqs, ar, ai, cp, sp);
-  // bhat = (nu_x - i nu_y)/|nu_perp|
-  R mag;
-  const C bhat = unit_dir(mkc((R)ps * a.pix, -(R)qs * a.piy), mag);
-  C K = cmul(__ldg(a.kx + p), __ldg(a.ky + q));
+  const ModeEntry<R> m = load_mode(a.mt, aps * (a.NY / 2 + 1) + aqs);
+  const C bhat = mkc(ps < 0 ? -m.bx : m.bx, qs < 0 ? m.by : -m.by);
+  C K = mkc(m.kr, m.ki);
   if (a.axis == 2) K = cmul(K, __ldg(a.kz + r));
-  apply_spin2<R>(v, mkc(ar, ai), bhat, cp, sp, K);
+  apply_spin2<R>(v, mkc(m.ar, m.ai), bhat, m.cp, m.sp, K);
 }
 
 template <typename R, int N, int E>

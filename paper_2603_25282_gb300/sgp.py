@@ -82,6 +82,8 @@ def lib():
         "sgp_synchronize": (I, [P]),
         "sgp_launch_count": (LL, [P]),
         "sgp_destroy": (I, [P]),
+        "sgp_set_profiling": (I, [P, I]),
+        "sgp_get_profile": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -185,6 +187,21 @@ def launch_count(ctx):
     return int(lib().sgp_launch_count(ctx))
 
 
+PROFILE_KINDS = ("xpass", "linepass_y", "linepass_z", "tables", "observables", "other")
+
+
+def set_profiling(ctx, enable):
+    _check(lib().sgp_set_profiling(ctx, int(bool(enable))), ctx)
+
+
+def get_profile(ctx):
+    """{kind: (launches, device ms)} since profiling was enabled."""
+    n = (ctypes.c_longlong * 6)()
+    ms = (ctypes.c_double * 6)()
+    _check(lib().sgp_get_profile(ctx, n, ms), ctx)
+    return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(PROFILE_KINDS)}
+
+
 def destroy(ctx):
     if ctx:
         _check(lib().sgp_destroy(ctx), None)
@@ -238,6 +255,12 @@ class Context:
 
     def launch_count(self):
         return launch_count(self.handle)
+
+    def set_profiling(self, enable):
+        set_profiling(self.handle, enable)
+
+    def get_profile(self):
+        return get_profile(self.handle)
 
     def close(self):
         if self.handle:
