@@ -30,10 +30,11 @@ const double kB2 = -kCbrt2 / (2.0 - kCbrt2);
 // ----------------------------------------------------------------------------
 // Rounding of an FP64 complex target to the working precision.  For FP32
 // the 5x5 neighbourhood (+-2 ulp per coordinate) of the rounded pair is
-// searched for the smallest |z - target| + ||z| - |target||: the factors are
-// applied in every step, so a modulus error of the stored value would turn
-// into a steady drift of the mass.
-__device__ inline void store_pair(double tx, double ty, float* ox, float* oy) {
+// searched for the smallest ||z| - |target|| + wz |z - target| (relative).
+// Twiddles use wz = 0.02: the inverse transform applies conj(W) on the same
+// path as the forward W, so only |W| enters the round trip and a modulus
+// error would otherwise accumulate over the steps.
+__device__ inline void store_pair_w(double tx, double ty, double wz, float* ox, float* oy) {
   const double m = sqrt(tx * tx + ty * ty);
   float xs[5], ys[5];
   xs[2] = (float)tx;
@@ -48,7 +49,7 @@ __device__ inline void store_pair(double tx, double ty, float* ox, float* oy) {
       const double x = xs[a], y = ys[b];
       const double dz = sqrt((x - tx) * (x - tx) + (y - ty) * (y - ty));
       const double dm = fabs(sqrt(x * x + y * y) - m);
-      const double sc = dz + dm;
+      const double sc = dm + wz * dz;
       if (sc < best) {
         best = sc;
         *ox = xs[a];
@@ -56,26 +57,37 @@ __device__ inline void store_pair(double tx, double ty, float* ox, float* oy) {
       }
     }
 }
-__device__ inline void store_pair(double tx, double ty, double* ox, double* oy) {
+__device__ inline void store_pair_w(double tx, double ty, double, double* ox, double* oy) {
   *ox = tx;
   *oy = ty;
 }
 
-// W_N^k = exp(-2 pi i k / N), k < N.
-template <typename R>
-__global__ void k_twiddles(int N, cplx<R>* out) {
+// W_N^k = exp(-2 pi i k / N), k < N, as hi + lo in FP32 (see TwE).
+__global__ void k_twiddles_f32(int N, TwE<float>* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   double s, c;
   sincospi(-2.0 * (double)k / (double)N, &s, &c);
-  R x, y;
-  store_pair(c, s, &x, &y);
-  out[k] = mkc(x, y);
+  const float hx = (float)c, hy = (float)s;
+  out[k] = TwE<float>{make_float2(hx, hy), make_float2((float)(c - hx), (float)(s - hy))};
+}
+__global__ void k_twiddles_f64(int N, TwE<double>* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)N, &s, &c);
+  out[k] = TwE<double>{make_double2(c, s)};
 }
 
 // Per-mode table of the linear flow over delta (Sec. 3.1, Eq. (sl1)), one
-// entry per (|p|, |q|) in the layout MT_* of sgp_kernels.cuh; the angles are
-// formed and the exponentials evaluated in FP64.  kz[r] = exp(-i nu_z^2 d/2)/NZ.
+// entry per (|p|, |q|) in the layout MT_* of sgp_kernels.cuh.  The angles are
+// formed and the exponentials evaluated in FP64, and the small quantities
+// exp(-i chi) - 1, ahat - 1, cp - 1 are written without cancellation:
+//   exp(-i chi) - 1 = (-2 sin^2(chi/2), -sin chi),
+//   U11 = c - i s Omega/lambda (c, s = cos, sin of delta lambda/2),
+//   cp - 1 = -s^2 gamma^2 |nu_perp|^2 / lambda^2 / (1 + cp),
+//   ahat - 1 = (c - cp - i s Omega/lambda)/cp,  c - cp = -s^2 Omega^2/lambda^2/(c + cp).
+// kz[r] = exp(-i nu_z^2 delta/2) - 1.
 template <typename R>
 __global__ void k_linear_tables(double delta, double omega, double gamma, int NX, int NY,
                                 int NZ, double Lx, double Ly, double Lz, R* mt, cplx<R>* kz) {
@@ -87,38 +99,44 @@ __global__ void k_linear_tables(double delta, double omega, double gamma, int NX
     const double nup = kPi * ap / Lx, nuq = kPi * aq / Ly;
     const double nperp = sqrt(nup * nup + nuq * nuq);
     const double lamb = sqrt(omega * omega + gamma * gamma * nperp * nperp);
-    double ar = 1.0, ai = 0.0, cp = 1.0, sp = 0.0;
+    double am1r = 0.0, am1i = 0.0, cm1 = 0.0, sp = 0.0;
     if (lamb > 0.0) {
       double sn, cs;
       sincos(0.5 * delta * lamb, &sn, &cs);
-      const double ur = cs, ui = -sn * omega / lamb;
-      cp = sqrt(ur * ur + ui * ui);
+      const double so = sn * omega / lamb;          // s Omega / lambda
+      const double sg = sn * gamma * nperp / lamb;  // s gamma |nu_perp| / lambda
+      const double cp = sqrt(cs * cs + so * so);
+      cm1 = -(sg * sg) / (1.0 + cp);
+      const double cmc = cs > 0.0 ? -(so * so) / (cs + cp) : cs - cp;
       if (cp > 0.0) {
-        ar = ur / cp;
-        ai = ui / cp;
+        am1r = cmc / cp;
+        am1i = -so / cp;
       }
-      sp = sn * gamma * nperp / lamb;
+      sp = sg;
     }
-    double ks, kc;
-    sincos(-0.5 * (nup * nup + nuq * nuq) * delta, &ks, &kc);
-    const double inv = 1.0 / ((double)NX * (double)NY);
+    const double chi = 0.5 * (nup * nup + nuq * nuq) * delta;
+    double sh, ch;
+    sincos(0.5 * chi, &sh, &ch);
     R* e = mt + (size_t)MT_STRIDE * id;
-    store_pair(kc * inv, ks * inv, &e[MT_KR], &e[MT_KI]);
-    store_pair(ar, ai, &e[MT_AR], &e[MT_AI]);
-    store_pair(cp, sp, &e[MT_CP], &e[MT_SP]);
+    e[MT_KHR] = (R)(-2.0 * sh * sh);
+    e[MT_KHI] = (R)(-2.0 * sh * ch);
+    e[MT_AM1R] = (R)am1r;
+    e[MT_AM1I] = (R)am1i;
+    e[MT_CM1] = (R)cm1;
+    e[MT_SP] = (R)sp;
     if (nperp > 0.0)
-      store_pair(nup / nperp, nuq / nperp, &e[MT_BX], &e[MT_BY]);
-    else
-      store_pair(1.0, 0.0, &e[MT_BX], &e[MT_BY]);
+      store_pair_w(nup / nperp, nuq / nperp, 0.02, &e[MT_BX], &e[MT_BY]);
+    else {
+      e[MT_BX] = (R)1;
+      e[MT_BY] = (R)0;
+    }
   }
   if (id < NZ) {
     const int ks_ = id < NZ / 2 ? id : id - NZ;
     const double nu = kPi * ks_ / Lz;
-    double sn, cs;
-    sincos(-0.5 * nu * nu * delta, &sn, &cs);
-    R x, y;
-    store_pair(cs / NZ, sn / NZ, &x, &y);
-    kz[id] = mkc(x, y);
+    double sh, ch;
+    sincos(0.25 * nu * nu * delta, &sh, &ch);
+    kz[id] = mkc((R)(-2.0 * sh * sh), (R)(-2.0 * sh * ch));
   }
 }
 
@@ -283,7 +301,7 @@ template <typename R>
 sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
   XPassArgs<R> a{};
   a.field = (cplx<R>*)c->field;
-  a.tw = (const cplx<R>*)c->tw[0];
+  a.tw = (const TwE<R>*)c->tw[0];
   a.ntot = c->ntot;
   a.rows = c->n[1] * c->n[2];
   a.ny = c->n[1];
@@ -315,7 +333,7 @@ template <typename R>
 sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
   LPassArgs<R> a{};
   a.field = (cplx<R>*)c->field;
-  a.tw = (const cplx<R>*)c->tw[axis];
+  a.tw = (const TwE<R>*)c->tw[axis];
   a.ntot = c->ntot;
   a.nx = c->n[0];
   const long long nxy = (long long)c->n[0] * c->n[1];
@@ -336,6 +354,11 @@ sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
   if (t) {
     a.mt = (const R*)t->mt;
     a.kz = (const cplx<R>*)t->kz;
+  }
+  {
+    const double inv = 1.0 / ((double)c->n[0] * c->n[1] * (c->dim == 3 ? c->n[2] : 1));
+    a.inv_hi = (R)inv;
+    a.inv_lo = (R)(inv - (double)a.inv_hi);
   }
   c->launches++;
   ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
@@ -457,7 +480,7 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
   ax.partials = c->partials;
   ax.nblocks = nbx;
   ax.field = (const cplx<R>*)c->field;
-  ax.tw = (const cplx<R>*)c->tw[0];
+  ax.tw = (const TwE<R>*)c->tw[0];
   ax.dnu = (R)(kPi / c->L[0] / NX);
   ax.NX = NX;
   c->launches++;
@@ -475,7 +498,7 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
     ObsLArgs<R> al{};
     static_cast<ObsArgsBase&>(al) = static_cast<const ObsArgsBase&>(ax);
     al.field = (const cplx<R>*)c->field;
-    al.tw = (const cplx<R>*)c->tw[axis];
+    al.tw = (const TwE<R>*)c->tw[axis];
     al.nx = NX;
     const long long nxy = (long long)c->n[0] * c->n[1];
     int planes;
@@ -618,12 +641,12 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
   if ((e = cudaMemsetAsync(c->field, 0, fbytes, c->stream)) != cudaSuccess)
     return bail(SGP_ECUDA, "field clear", e);
   for (int a = 0; a < dim; ++a) {
-    if ((e = cudaMalloc(&c->tw[a], (size_t)c->n[a] * c->elem)) != cudaSuccess)
+    if ((e = cudaMalloc(&c->tw[a], (size_t)c->n[a] * 16)) != cudaSuccess)
       return bail(SGP_ENOMEM, "twiddle allocation", e);
     if (prec == SGP_F32)
-      k_twiddles<float><<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (float2*)c->tw[a]);
+      k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (TwE<float>*)c->tw[a]);
     else
-      k_twiddles<double><<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (double2*)c->tw[a]);
+      k_twiddles_f64<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (TwE<double>*)c->tw[a]);
     c->launches++;
   }
   if ((e = cudaMalloc(&c->t_dev, sizeof(double))) != cudaSuccess)

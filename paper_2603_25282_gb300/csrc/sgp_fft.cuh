@@ -128,6 +128,46 @@ template <int DIR, typename C> __device__ __forceinline__ C rot_mi(C a) {
   return DIR < 0 ? cmulmi(a) : cmuli(a);
 }
 
+// x * k for the butterfly constants sqrt(1/2) and sqrt(3)/2.  In FP32 the
+// constant is the unevaluated sum hi + lo and the product is formed as
+// fma(x, hi, x*lo): one rounding of x*(hi + lo).  A plain rounded constant
+// (or fma(x, lo, x*hi), whose small term is lost against the rounded large
+// product) biases every forward/inverse pair the same way: with k^2 = 1/2
+// rounded, each radix-8 butterfly would shrink the norm by ~1e-8 and a
+// long run would lose mass steadily.
+__device__ __forceinline__ float mul_rt_half(float x) {
+  return fmaf(x, 0.7071067690849304f, x * 1.21016175e-08f);
+}
+__device__ __forceinline__ double mul_rt_half(double x) { return x * 0.70710678118654752440; }
+__device__ __forceinline__ float mul_rt3_half(float x) {
+  return fmaf(x, 0.8660253882408142f, x * 1.5543625e-08f);
+}
+__device__ __forceinline__ double mul_rt3_half(double x) { return x * 0.86602540378443864676; }
+
+// Twiddle table entries.  FP32: W = hi + lo (both float2), applied with
+// tw_mul as one rounding of the product with the unevaluated sum, so the
+// table's rounding does not shrink or grow every forward/inverse pair; FP64:
+// the rounded value alone.
+template <typename R> struct TwE;
+template <> struct TwE<float> { float2 hi, lo; };
+template <> struct TwE<double> { double2 hi; };
+
+__device__ __forceinline__ TwE<float> tw_conj(TwE<float> t) {
+  return TwE<float>{make_float2(t.hi.x, -t.hi.y), make_float2(t.lo.x, -t.lo.y)};
+}
+__device__ __forceinline__ TwE<double> tw_conj(TwE<double> t) {
+  return TwE<double>{make_double2(t.hi.x, -t.hi.y)};
+}
+__device__ __forceinline__ float2 tw_mul(float2 x, TwE<float> w) {
+  const float sr = fmaf(x.x, w.lo.x, -x.y * w.lo.y);
+  const float si = fmaf(x.x, w.lo.y, x.y * w.lo.x);
+  return make_float2(fmaf(x.x, w.hi.x, fmaf(-x.y, w.hi.y, sr)),
+                     fmaf(x.x, w.hi.y, fmaf(x.y, w.hi.x, si)));
+}
+__device__ __forceinline__ double2 tw_mul(double2 x, TwE<double> w) {
+  return make_double2(fma(x.x, w.hi.x, -x.y * w.hi.y), fma(x.x, w.hi.y, x.y * w.hi.x));
+}
+
 template <int RD, int DIR, typename C> struct Dft;
 
 template <int DIR, typename C> struct Dft<2, DIR, C> {
@@ -151,8 +191,6 @@ template <int DIR, typename C> struct Dft<4, DIR, C> {
 
 template <int DIR, typename C> struct Dft<8, DIR, C> {
   __device__ __forceinline__ static void run(C (&x)[8]) {
-    typedef decltype(x[0].x) R;
-    const R h = (R)0.70710678118654752440;
     C e[4] = {x[0], x[2], x[4], x[6]};
     C o[4] = {x[1], x[3], x[5], x[7]};
     Dft<4, DIR, C>::run(e);
@@ -160,13 +198,13 @@ template <int DIR, typename C> struct Dft<8, DIR, C> {
     // twiddles W8^k, k = 1..3 (forward: (1-i)/sqrt2, -i, (-1-i)/sqrt2)
     C o1 = o[1], o2 = o[2], o3 = o[3];
     if (DIR < 0) {
-      o1 = mkc((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+      o1 = mkc(mul_rt_half(o1.x + o1.y), mul_rt_half(o1.y - o1.x));
       o2 = cmulmi(o2);
-      o3 = mkc((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+      o3 = mkc(mul_rt_half(o3.y - o3.x), -mul_rt_half(o3.x + o3.y));
     } else {
-      o1 = mkc((o1.x - o1.y) * h, (o1.y + o1.x) * h);
+      o1 = mkc(mul_rt_half(o1.x - o1.y), mul_rt_half(o1.y + o1.x));
       o2 = cmuli(o2);
-      o3 = mkc(-(o3.x + o3.y) * h, (o3.x - o3.y) * h);
+      o3 = mkc(-mul_rt_half(o3.x + o3.y), mul_rt_half(o3.x - o3.y));
     }
     x[0] = cadd(e[0], o[0]);
     x[4] = csub(e[0], o[0]);
@@ -182,12 +220,12 @@ template <int DIR, typename C> struct Dft<8, DIR, C> {
 template <int DIR, typename C> struct Dft<3, DIR, C> {
   __device__ __forceinline__ static void run(C (&x)[3]) {
     typedef decltype(x[0].x) R;
-    const R s3 = (R)0.86602540378443864676;
     C t = cadd(x[1], x[2]);
     C u = csub(x[1], x[2]);
     C m = mkc(fma(t.x, (R)-0.5, x[0].x), fma(t.y, (R)-0.5, x[0].y));
     // forward: X1 = m - i s3 u, X2 = m + i s3 u
-    C iu = DIR < 0 ? mkc(u.y * s3, -u.x * s3) : mkc(-u.y * s3, u.x * s3);
+    const R su_x = mul_rt3_half(u.x), su_y = mul_rt3_half(u.y);
+    C iu = DIR < 0 ? mkc(su_y, -su_x) : mkc(-su_y, su_x);
     x[0] = cadd(x[0], t);
     x[1] = cadd(m, iu);
     x[2] = csub(m, iu);
@@ -197,15 +235,17 @@ template <int DIR, typename C> struct Dft<3, DIR, C> {
 template <int DIR, typename C> struct Dft<6, DIR, C> {
   __device__ __forceinline__ static void run(C (&x)[6]) {
     typedef decltype(x[0].x) R;
-    const R s3 = (R)0.86602540378443864676;
     C e[3] = {x[0], x[2], x[4]};
     C o[3] = {x[1], x[3], x[5]};
     Dft<3, DIR, C>::run(e);
     Dft<3, DIR, C>::run(o);
-    // W6^1 = 1/2 -+ i s3, W6^2 = -1/2 -+ i s3
+    // W6^1 = 1/2 -+ i s3, W6^2 = -1/2 -+ i s3 (s3 = sqrt(3)/2):
+    // o * (+-1/2 + i sg s3) = (+-o.x/2 - sg s3 o.y, +-o.y/2 + sg s3 o.x)
     const R sg = DIR < 0 ? (R)-1 : (R)1;
-    C w1 = mkc((R)0.5, sg * s3), w2 = mkc((R)-0.5, sg * s3);
-    C o1 = cmul(o[1], w1), o2 = cmul(o[2], w2);
+    const R a1x = mul_rt3_half(o[1].x), a1y = mul_rt3_half(o[1].y);
+    const R a2x = mul_rt3_half(o[2].x), a2y = mul_rt3_half(o[2].y);
+    C o1 = mkc((R)0.5 * o[1].x - sg * a1y, (R)0.5 * o[1].y + sg * a1x);
+    C o2 = mkc((R)-0.5 * o[2].x - sg * a2y, (R)-0.5 * o[2].y + sg * a2x);
     x[0] = cadd(e[0], o[0]);
     x[3] = csub(e[0], o[0]);
     x[1] = cadd(e[1], o1);
@@ -219,13 +259,13 @@ template <int DIR, typename C> struct Dft<6, DIR, C> {
 // Stockham stages over NC components held in registers
 // ----------------------------------------------------------------------------
 // v[c][e]: element i + T*e of component c's line.  tw: W_N^k = exp(-2 pi i k/N),
-// k = 0..N-1, in shared memory.  b0/b1: two padded exchange lines of this
+// k = 0..N-1 (TwE entries), in shared memory.  b0/b1: two padded exchange lines of this
 // thread group.  DIR = -1 forward, +1 inverse.  Every thread of the CTA must
 // call this (it contains __syncthreads).
 template <typename R, int N, int E, int DIR, int NC, int S, int NS>
 struct FftStages {
   typedef cplx<R> C;
-  __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const C* tw,
+  __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const TwE<R>* tw,
                                              C* b0, C* b1) {
     constexpr int RD = radix_at(N, E, S);
     if constexpr (RD > 0) {
@@ -233,16 +273,15 @@ struct FftStages {
       constexpr int B = E / RD;
       constexpr bool LAST = (NS * RD == N);
       constexpr int TSTEP = N / (NS * RD);
-      C w[B][RD];
+      TwE<R> w[B][RD];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        w[k][0] = mkc((R)1, (R)0);
         if constexpr (NS > 1) {
           const int j = (i + T * k) % NS;
 #pragma unroll
           for (int r = 1; r < RD; ++r) {
-            C t = tw[j * r * TSTEP];
-            w[k][r] = DIR < 0 ? t : cconj(t);
+            const TwE<R> t = tw[j * r * TSTEP];
+            w[k][r] = DIR < 0 ? t : tw_conj(t);
           }
         }
       }
@@ -256,7 +295,7 @@ struct FftStages {
           for (int r = 0; r < RD; ++r) {
             x[r] = v[c][k + r * B];
             if constexpr (NS > 1) {
-              if (r > 0) x[r] = cmul(x[r], w[k][r]);
+              if (r > 0) x[r] = tw_mul(x[r], w[k][r]);
             }
           }
           Dft<RD, DIR, C>::run(x);
@@ -291,7 +330,7 @@ struct FftStages {
 template <typename R, int N, int E, int NC, int S, int NS>
 struct FftStagesAdj {
   typedef cplx<R> C;
-  __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const C* tw,
+  __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const TwE<R>* tw,
                                              C* b0, C* b1) {
     constexpr int RD = radix_at(N, E, S);
     if constexpr (RD > 0) {
@@ -301,14 +340,13 @@ struct FftStagesAdj {
       constexpr int B = E / RD;
       constexpr bool LAST = (NS * RD == N);
       constexpr int TSTEP = N / (NS * RD);
-      C w[B][RD];
+      TwE<R> w[B][RD];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        w[k][0] = mkc((R)1, (R)0);
         if constexpr (NS > 1) {
           const int j = (i + T * k) % NS;
 #pragma unroll
-          for (int r = 1; r < RD; ++r) w[k][r] = cconj(tw[j * r * TSTEP]);
+          for (int r = 1; r < RD; ++r) w[k][r] = tw_conj(tw[j * r * TSTEP]);
         }
       }
 #pragma unroll
@@ -335,7 +373,7 @@ struct FftStagesAdj {
 #pragma unroll
           for (int r = 0; r < RD; ++r) {
             if constexpr (NS > 1) {
-              if (r > 0) x[r] = cmul(x[r], w[k][r]);
+              if (r > 0) x[r] = tw_mul(x[r], w[k][r]);
             }
             v[c][k + r * B] = x[r];
           }
@@ -349,7 +387,7 @@ struct FftStagesAdj {
 // unnormalised) transform of NC lines held in layout A.
 template <typename R, int N, int E, int DIR, int NC>
 __device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i,
-                                          const cplx<R>* tw, cplx<R>* b0,
+                                          const TwE<R>* tw, cplx<R>* b0,
                                           cplx<R>* b1) {
   static_assert(plan_ok(N, E), "no radix plan for this (N, E)");
   // the previous user of the exchange buffers may still be reading

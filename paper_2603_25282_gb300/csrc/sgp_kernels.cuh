@@ -32,7 +32,7 @@ enum { LP_FWD = 1, LP_MIX = 2, LP_INV = 4 };
 template <typename R>
 struct XPassArgs {
   cplx<R>* field;        // [batch][5][ntot]
-  const cplx<R>* tw;     // W_Nx^k, k < Nx
+  const TwE<R>* tw;      // W_Nx^k, k < Nx
   long long ntot;        // nx*ny*nz
   int rows;              // ny*nz rows per member
   int ny;
@@ -48,7 +48,7 @@ struct XPassArgs {
 template <typename R>
 struct LPassArgs {
   cplx<R>* field;
-  const cplx<R>* tw;          // W_N^k along the line axis
+  const TwE<R>* tw;           // W_N^k along the line axis
   long long ntot;
   int nx;                     // number of x positions (tile axis)
   long long line_stride;      // element stride along the line
@@ -58,84 +58,101 @@ struct LPassArgs {
   int NX, NY;                 // grid sizes along x and y (mode indices)
   // per-mode table over (|p|, |q|), MT_STRIDE values per entry (see MT_*)
   const R* mt;
-  const cplx<R>* kz;          // exp(-i nu_z^2 d/2)/NZ (3D only)
+  const cplx<R>* kz;          // exp(-i nu_z^2 d/2) - 1 (3D only)
+  R inv_hi, inv_lo;           // 1/(NX NY [NZ]) as an unevaluated sum hi + lo
 };
 
 // Entry layout of the per-mode table of the linear flow over delta, indexed
 // by (|p|, |q|) (everything below depends on nu_x^2 and nu_y^2 only):
-//   K     = exp(-i (nu_x^2 + nu_y^2) delta/2) / (NX NY)
-//   ahat  = U11/|U11|, cp = |U11|, sp = signed |U12| of
-//           U = exp(i delta lambda n.sigma/2), lambda^2 = Omega^2 + gamma^2 |nu_perp|^2
+//   khat  = exp(-i (nu_x^2 + nu_y^2) delta/2) - 1
+//   am1   = ahat - 1, cm1 = cp - 1, sp: U11 = cp*ahat (|ahat| = 1) and
+//           U12 = sp*bhat of U = exp(i delta lambda n.sigma/2),
+//           lambda^2 = Omega^2 + gamma^2 |nu_perp|^2
 //   (bx, by) = (|nu_x|, |nu_y|)/|nu_perp|; the mode direction is
 //           bhat = (sign(p) bx, -sign(q) by) = (nu_x - i nu_y)/|nu_perp|.
-enum { MT_KR = 0, MT_KI, MT_AR, MT_AI, MT_CP, MT_SP, MT_BX, MT_BY, MT_STRIDE };
+// The small quantities khat, am1, cm1, sp are formed in FP64 without
+// cancellation, so the flow is applied as v + (increment) with the increment
+// accurate to its own rounding (see apply_flow_increment).
+enum { MT_KHR = 0, MT_KHI, MT_AM1R, MT_AM1I, MT_CM1, MT_SP, MT_BX, MT_BY, MT_STRIDE };
 
 // ----------------------------------------------------------------------------
-// spin-2 image of an SU(2) element in the factorised form
+// spin-2 image of an SU(2) element, applied as an increment
 // ----------------------------------------------------------------------------
-// v <- K * diag(w^m) d(cp, sp) diag(z^m) v, m = 2, 1, 0, -1, -2.
+// e = (D - I) v for D = diag(w^m) d(cp, sp) diag(z^m), w = ahat*bhat,
+// z = ahat*conj(bhat) (|ahat| = |bhat| = 1), given am1 = ahat - 1,
+// cm1 = cp - 1 and sp (cp^2 + sp^2 = 1).  Written as
+//   D - I = diag(w^m) (d - I) diag(z^m) + diag(ahat^(2m) - 1),
+// where every entry of d - I and every ahat^(2m) - 1 is built from the small
+// inputs without cancellation, so e carries an error relative to its own
+// size: the rounding of the (fixed) factors does not accumulate over steps.
 template <typename R>
-__device__ __forceinline__ void apply_spin2(cplx<R> (&v)[5], cplx<R> ahat,
-                                            cplx<R> bhat, R cp, R sp,
-                                            cplx<R> K) {
+__device__ __forceinline__ void spin2_increment(const cplx<R> (&v)[5], cplx<R> am1,
+                                                cplx<R> bhat, R cm1, R sp,
+                                                cplx<R> (&e)[5]) {
   typedef cplx<R> C;
-  const R r6 = (R)2.44948974278317809820;   // sqrt(6)
+  const R r6 = (R)2.44948974278317809820;
+  const C ahat = mkc((R)1 + am1.x, am1.y);
+  // ahat^2 - 1 = am1 (2 + am1), ahat^4 - 1 = g2 (2 + g2)
+  const C g2 = cmul(am1, mkc((R)2 + am1.x, am1.y));
+  const C g4 = cmul(g2, mkc((R)2 + g2.x, g2.y));
   const C w = cmul(ahat, bhat);
   const C z = cmulc(ahat, bhat);
   const C z2 = cmul(z, z);
-  // u = diag(z^m) v
-  C u0 = cmul(z2, v[0]);
-  C u1 = cmul(z, v[1]);
-  C u2 = v[2];
-  C u3 = cmulc(v[3], z);
-  C u4 = cmulc(v[4], z2);
-  // real spin-2 rotation matrix d(c, s) (rows/cols m = 2..-2)
-  const R c = cp, s = sp;
-  const R c2 = c * c, s2 = s * s, cs = c * s;
-  const R A = c2 * c2, B = s2 * s2;
-  const R P = (R)2 * c2 * cs;        // 2 c^3 s
-  const R Qv = (R)2 * cs * s2;       // 2 c s^3
-  const R Rv = r6 * c2 * s2;         // sqrt6 c^2 s^2
-  const R Sv = r6 * cs * (c2 - s2);  // sqrt6 c s (c^2 - s^2)
-  const R T1 = c2 * (c2 - (R)3 * s2);
+  const C u0 = cmul(z2, v[0]);
+  const C u1 = cmul(z, v[1]);
+  const C u2 = v[2];
+  const C u3 = cmulc(v[3], z);
+  const C u4 = cmulc(v[4], z2);
+  // d(c, s) - I with c = 1 + cm1, s = sp
+  const R c = (R)1 + cm1, s = sp;
+  const R c2m1 = cm1 * ((R)2 + cm1);            // c^2 - 1
+  const R c2 = (R)1 + c2m1, s2 = s * s, cs = c * s;
+  const R Am1 = c2m1 * (c2 + (R)1);             // c^4 - 1
+  const R B = s2 * s2;
+  const R P = (R)2 * c2 * cs;                   // 2 c^3 s
+  const R Qv = (R)2 * cs * s2;                  // 2 c s^3
+  const R Rv = r6 * c2 * s2;                    // sqrt6 c^2 s^2
+  const R Sv = r6 * cs * (c2 - s2);             // sqrt6 c s (c^2 - s^2)
+  const R T1m1 = Am1 - (R)3 * c2 * s2;          // c^2 (c^2 - 3 s^2) - 1
   const R T2 = s2 * ((R)3 * c2 - s2);
-  const R M0 = A + B - (R)4 * c2 * s2;
-  C o0 = cscale(u0, A);
+  const R M0m1 = Am1 + B - (R)4 * c2 * s2;      // c^4 + s^4 - 4 c^2 s^2 - 1
+  C o0 = cscale(u0, Am1);
   o0 = caxpy(o0, u1, P);
   o0 = caxpy(o0, u2, Rv);
   o0 = caxpy(o0, u3, Qv);
   o0 = caxpy(o0, u4, B);
   C o1 = cscale(u0, -P);
-  o1 = caxpy(o1, u1, T1);
+  o1 = caxpy(o1, u1, T1m1);
   o1 = caxpy(o1, u2, Sv);
   o1 = caxpy(o1, u3, T2);
   o1 = caxpy(o1, u4, Qv);
   C o2 = cscale(u0, Rv);
   o2 = caxpy(o2, u1, -Sv);
-  o2 = caxpy(o2, u2, M0);
+  o2 = caxpy(o2, u2, M0m1);
   o2 = caxpy(o2, u3, Sv);
   o2 = caxpy(o2, u4, Rv);
   C o3 = cscale(u0, -Qv);
   o3 = caxpy(o3, u1, T2);
   o3 = caxpy(o3, u2, -Sv);
-  o3 = caxpy(o3, u3, T1);
+  o3 = caxpy(o3, u3, T1m1);
   o3 = caxpy(o3, u4, P);
   C o4 = cscale(u0, B);
   o4 = caxpy(o4, u1, -Qv);
   o4 = caxpy(o4, u2, Rv);
   o4 = caxpy(o4, u3, -P);
-  o4 = caxpy(o4, u4, A);
-  // v = K diag(w^m) o
-  const C Kw = cmul(K, w);
-  const C Kw2 = cmul(Kw, w);
-  const C Kwc = cmulc(K, w);
-  const C Kwc2 = cmulc(Kwc, w);
-  v[0] = cmul(Kw2, o0);
-  v[1] = cmul(Kw, o1);
-  v[2] = cmul(K, o2);
-  v[3] = cmul(Kwc, o3);
-  v[4] = cmul(Kwc2, o4);
+  o4 = caxpy(o4, u4, Am1);
+  const C w2 = cmul(w, w);
+  e[0] = cadd(cmul(w2, o0), cmul(g4, v[0]));
+  e[1] = cadd(cmul(w, o1), cmul(g2, v[1]));
+  e[2] = o2;
+  e[3] = cadd(cmulc(o3, w), cmulc(v[3], g2));     // conj(w) o3 + (conj(ahat^2) - 1) v3
+  e[4] = cadd(cmulc(o4, w2), cmulc(v[4], g4));
 }
+
+// x * c for a constant given as the unevaluated sum hi + lo (FP32), so the
+// product carries only its own rounding; plain product in FP64.
+__device__ __forceinline__ float mulc2(float x, float hi, float lo) { return fmaf(x, hi, x * lo); }
+__device__ __forceinline__ double mulc2(double x, double hi, double lo) { return x * hi; }
 
 __device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sincos(a, s, c); }
@@ -181,56 +198,65 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   // A00 = (2 p2 m2 - 2 p1 m1 + p0^2)/sqrt5
   C A00 = csub(cmul(v[0], v[4]), cmul(v[1], v[3]));
   A00 = cscale(cadd(cscale(A00, (R)2), cmul(v[2], v[2])), rs5);
-  // singlet-pair rotation: cos(c2 S d) Psi + i sin(c2 S d)/S (rho/5 Psi - A00 A conj(Psi))
+  // (1) singlet-pair rotation, as the increment db of
+  //     b = cos(c2 S d) Psi + i sin(c2 S d)/S (rho/5 Psi - A00 A conj(Psi)),
+  //     cos - 1 = -2 sin^2(c2 S d / 2)
   const R S2 = rho * rho * (R)0.04 - cabs2(A00) * (R)0.2;
   const R S = S2 > (R)0 ? sqrt(S2) : (R)0;
-  R sn, cs;
-  sincos_r(c2 * S * delta, &sn, &cs);
-  const R sinc = S > (R)0 ? sn / S : c2 * delta;
+  R sh1, ch1;
+  sincos_r((R)0.5 * c2 * S * delta, &sh1, &ch1);
+  const R cm1 = (R)-2 * sh1 * sh1;
+  const R sinc = S > (R)0 ? (R)2 * sh1 * ch1 / S : c2 * delta;
   const R r5 = rho * (R)0.2;
-  // A conj(Psi) = (conj m2, -conj m1, conj p0, -conj p1, conj p2)/sqrt5
   const C As = cscale(A00, rs5);
-  C b[5];
+  C inc[5], b[5];
   {
+    // A conj(Psi) = (conj m2, -conj m1, conj p0, -conj p1, conj p2)/sqrt5
     const C ac[5] = {cconj(v[4]), cneg(cconj(v[3])), cconj(v[2]),
                      cneg(cconj(v[1])), cconj(v[0])};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       C t = csub(cscale(v[k], r5), cmul(As, ac[k]));    // rho/5 Psi - A00 A conj(Psi)
-      t = cscale(cmuli(t), sinc);
-      b[k] = cadd(cscale(v[k], cs), t);
+      inc[k] = cadd(cscale(v[k], cm1), cscale(cmuli(t), sinc));
+      b[k] = cadd(v[k], inc[k]);
     }
   }
-  // spin rotation exp(-i c1 d F.f) = spin-2 image of cos(k/2) - i sin(k/2) Fhat.sigma,
-  // k = c1 d |F|:  U11 = cos(k/2) - i q Fz, U12 = -i q conj(F+), q = sin(k/2)/|F|
-  const R F2 = cabs2(Fp) + Fz * Fz;
-  R q, ch;
+  // (2) spin rotation exp(-i c1 d F.f): spin-2 image of
+  //     U = cos(k/2) - i sin(k/2) Fhat.sigma, k = c1 d |F|:
+  //     U11 = cos(k/2) - i q Fz, U12 = -i q conj(F+), q = sin(k/2)/|F|.
+  //     ahat - 1 and cp - 1 are formed without cancellation:
+  //       cp - 1 = -q^2 |F+|^2 / (1 + cp),  ahat - 1 = (cos - cp - i q Fz)/cp,
+  //       cos - cp = -q^2 Fz^2 / (cos + cp)
+  const R Fp2 = cabs2(Fp);
+  const R F2 = Fp2 + Fz * Fz;
   if (F2 > (R)0) {
     const R Fn = sqrt(F2);
-    R sh;
+    R sh, ch;
     sincos_r((R)0.5 * c1 * delta * Fn, &sh, &ch);
-    q = sh / Fn;
-  } else {
-    ch = (R)1;
-    q = (R)0;
-  }
-  const C U11 = mkc(ch, -q * Fz);
-  const C U12 = mkc(-q * Fp.y, -q * Fp.x);
-  R cp, sp;
-  const C ahat = unit_dir(U11, cp);
-  const C bhat = unit_dir(U12, sp);
-  {
-    // cp^2 + sp^2 = 1 to rounding (d(cp, sp) is homogeneous of degree 4)
-    const R nrm = rsqrt_r(fma(cp, cp, sp * sp));
-    cp *= nrm;
-    sp *= nrm;
-  }
-  // scalar phase exp(-i d (V + (c0 + c2/5) rho))
-  R ps, pc;
-  sincos_r(-delta * (V + c0p * rho), &ps, &pc);
+    const R q = sh / Fn;
+    const R qFz = q * Fz;
+    const R cp = sqrt(ch * ch + qFz * qFz);
+    const R cpm1 = -(q * q * Fp2) / ((R)1 + cp);
+    const R icp = (R)1 / cp;
+    const R cmc = ch > (R)0 ? -(qFz * qFz) / (ch + cp) : ch - cp;   // cos - cp
+    const C am1 = mkc(cmc * icp, -qFz * icp);
+    R mag;
+    const C bhat = unit_dir(mkc(-Fp.y, -Fp.x), mag);   // direction of -i conj(F+)
+    const R sp = q * mag;
+    C e[5];
+    spin2_increment<R>(b, am1, bhat, cpm1, sp, e);
 #pragma unroll
-  for (int k = 0; k < 5; ++k) v[k] = b[k];
-  apply_spin2<R>(v, ahat, bhat, cp, sp, mkc(pc, ps));
+    for (int k = 0; k < 5; ++k) {
+      inc[k] = cadd(inc[k], e[k]);
+      b[k] = cadd(b[k], e[k]);
+    }
+  }
+  // (3) scalar phase exp(-i d (V + (c0 + c2/5) rho)) - 1 = (-2 sin^2(ph/2), -sin(ph))
+  R sh3, ch3;
+  sincos_r((R)-0.5 * delta * (V + c0p * rho), &sh3, &ch3);
+  const C pm1 = mkc((R)-2 * sh3 * sh3, (R)2 * sh3 * ch3);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k] = cadd(v[k], cadd(inc[k], cmul(pm1, b[k])));
 }
 
 // ----------------------------------------------------------------------------
@@ -242,7 +268,7 @@ struct XCfg {
   static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
   static constexpr int THREADS = ROWS * T;
   static constexpr int LP = line_pad<R>(N);
-  static constexpr size_t SMEM = sizeof(cplx<R>) * (size_t)(N + 2 * ROWS * LP);
+  static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * ROWS * LP);
 };
 
 template <typename R, int N, int E>
@@ -252,8 +278,8 @@ k_xpass(XPassArgs<R> a) {
   typedef XCfg<R, N, E> Cfg;
   constexpr int T = Cfg::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* xb = tw + N;
+  TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
+  C* xb = reinterpret_cast<C*>(tw + N);
   __shared__ R s_rot[2];
   const int g = threadIdx.x / T;
   const int i = threadIdx.x - g * T;
@@ -317,10 +343,10 @@ struct LCfg {
   static constexpr int TILE = (512 / T) > TMAX ? TMAX : ((512 / T) < TMIN ? TMIN : (512 / T));
   static constexpr int THREADS = TILE * T;
   static constexpr int LP = line_pad<R>(N);
-  static constexpr size_t SMEM = sizeof(cplx<R>) * (size_t)(N + 2 * TILE * LP);
+  static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * TILE * LP);
 };
 
-template <typename R> struct ModeEntry { R kr, ki, ar, ai, cp, sp, bx, by; };
+template <typename R> struct ModeEntry { R khr, khi, am1r, am1i, cm1, sp, bx, by; };
 
 __device__ __forceinline__ ModeEntry<float> load_mode(const float* mt, int idx) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(mt) + 2 * idx);
@@ -333,7 +359,9 @@ __device__ __forceinline__ ModeEntry<double> load_mode(const double* mt, int idx
   return ModeEntry<double>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
 }
 
-// linear flow of one Fourier mode (p, q, r in FFT order)
+// linear flow of one Fourier mode (p, q, r in FFT order), including the
+// 1/(NX NY [NZ]) of the forward transforms:
+//   v <- (1 + khat) D v / N = (v + f) / N,  f = e + khat (v + e),  e = (D - I) v.
 template <typename R>
 __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
                                          int p, int q, int r) {
@@ -344,9 +372,19 @@ __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
   const int aqs = qs < 0 ? -qs : qs;
   const ModeEntry<R> m = load_mode(a.mt, aps * (a.NY / 2 + 1) + aqs);
   const C bhat = mkc(ps < 0 ? -m.bx : m.bx, qs < 0 ? m.by : -m.by);
-  C K = mkc(m.kr, m.ki);
-  if (a.axis == 2) K = cmul(K, __ldg(a.kz + r));
-  apply_spin2<R>(v, mkc(m.ar, m.ai), bhat, m.cp, m.sp, K);
+  C kh = mkc(m.khr, m.khi);
+  if (a.axis == 2) {
+    const C kz = __ldg(a.kz + r);       // (1 + kh)(1 + kz) - 1
+    kh = cadd(cadd(kh, kz), cmul(kh, kz));
+  }
+  C e[5];
+  spin2_increment<R>(v, mkc(m.am1r, m.am1i), bhat, m.cm1, m.sp, e);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const C x = cadd(v[k], e[k]);
+    const C t = cadd(v[k], cadd(e[k], cmul(kh, x)));
+    v[k] = mkc(mulc2(t.x, a.inv_hi, a.inv_lo), mulc2(t.y, a.inv_hi, a.inv_lo));
+  }
 }
 
 template <typename R, int N, int E>
@@ -357,8 +395,8 @@ k_linepass(LPassArgs<R> a) {
   constexpr int T = Cfg::T;
   constexpr int TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* xb = tw + N;
+  TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
+  C* xb = reinterpret_cast<C*>(tw + N);
   const int col = threadIdx.x % TILE;
   const int i = threadIdx.x / TILE;
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
@@ -429,7 +467,7 @@ constexpr int OBL_NT = 3;    // terms written by k_obs_line (kin, lz, soc)
 template <typename R>
 struct ObsXArgs : ObsArgsBase {
   const cplx<R>* field;
-  const cplx<R>* tw;
+  const TwE<R>* tw;
   R dnu;                 // pi/Lx / Nx (derivative factor with the 1/N of the forward transform)
   int NX;
 };
@@ -437,7 +475,7 @@ struct ObsXArgs : ObsArgsBase {
 template <typename R>
 struct ObsLArgs : ObsArgsBase {
   const cplx<R>* field;
-  const cplx<R>* tw;
+  const TwE<R>* tw;
   int nx;
   long long line_stride, plane_stride;
   int axis;              // 1: y lines, 2: z lines
@@ -477,8 +515,8 @@ k_obs_x(ObsXArgs<R> a) {
   typedef XCfg<R, N, E> Cfg;
   constexpr int T = Cfg::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* xb = tw + N;
+  TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
+  C* xb = reinterpret_cast<C*>(tw + N);
   __shared__ double red[32 * 10];
   const int g = threadIdx.x / T;
   const int i = threadIdx.x - g * T;
@@ -575,8 +613,8 @@ k_obs_line(ObsLArgs<R> a) {
   constexpr int T = Cfg::T;
   constexpr int TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* xb = tw + N;
+  TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
+  C* xb = reinterpret_cast<C*>(tw + N);
   __shared__ double red[32 * 3];
   const int col = threadIdx.x % TILE;
   const int i = threadIdx.x / TILE;
