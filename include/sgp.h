@@ -155,6 +155,38 @@ sgp_status sgp_substep(sgp_ctx* ctx, int kind, double delta);
  * filled) if any sum is NaN or Inf. */
 sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
 
+/* Allocation-free observables (no counterpart in the paper; a service of
+ * this library).  Computes the same quantities as sgp_observables for a
+ * field the caller already holds on the device, without a context and
+ * without allocating anything: no cudaMalloc, cudaFree or other allocating
+ * call is made.  It is meant for callers that cannot allocate device memory
+ * at this point: code whose device memory is entirely reserved by another
+ * allocator's pool, code on a latency-critical path where cudaMalloc's
+ * implicit device synchronisation is not acceptable, and code that only
+ * holds a device pointer to a field produced elsewhere.
+ *
+ * All scratch (per-block partial sums, FFT twiddles, final sums) lives in
+ * file-scope device arrays of fixed size that every GPU which loads the
+ * library keeps until the process exits.  Limits: each n[a] as in
+ * sgp_create_grid (<= 1024), batch <= 64, and at most 2^19 per-block partial
+ * sums (batch * ny * nz / rows-per-block * 13, e.g. batch 64 at 512^2 in
+ * FP32); larger requests return SGP_EINVAL with a message.
+ *
+ * Arguments: the grid and precision as in sgp_create_grid; p the
+ * parameters; t the time; field_dev a device pointer (on `device`) to
+ * batch*5*nz*ny*nx elements in the layout of sgp_set_state, read only;
+ * stream a cudaStream_t (or NULL); out[0..batch-1] host results.  The call
+ * synchronises `stream`.  The first call on a device looks up the device
+ * addresses of the scratch arrays (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call uses
+ * the same scratch and overwrites what the previous call left there, so
+ * calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
+sgp_status sgp_observables_static(int dim, const int* n, const double* L, int batch,
+                                  int prec, const sgp_params* p, double t,
+                                  const void* field_dev, int device, void* stream,
+                                  sgp_obs* out);
+
 /* Wait for all work issued on the context stream. */
 sgp_status sgp_synchronize(sgp_ctx* ctx);
 

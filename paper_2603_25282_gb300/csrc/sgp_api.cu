@@ -811,3 +811,220 @@ sgp_status sgp_destroy(sgp_ctx* c) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// allocation-free observables (sgp_observables_static)
+// ----------------------------------------------------------------------------
+// Fixed-size scratch in file-scope device arrays.  Host code must not use
+// these names as addresses: it looks the device addresses up with
+// cudaGetSymbolAddress (once per device) and passes them to the kernels.
+namespace {
+constexpr int kStaticMaxBatch = 64;
+constexpr size_t kStaticMaxPartials = (size_t)1 << 19;     // doubles
+constexpr int kStaticMaxN = 1024;
+
+static __device__ __align__(256) double g_static_partials[kStaticMaxPartials];
+static __device__ __align__(256) double g_static_sums[kStaticMaxBatch * OB_NT];
+static __device__ __align__(256) double2 g_static_tw[3 * kStaticMaxN];   // TwE: 16 B each
+
+struct StaticScratch {
+  double* partials = nullptr;
+  double* sums = nullptr;
+  void* tw = nullptr;
+};
+constexpr int kMaxDevices = 64;
+StaticScratch g_scratch[kMaxDevices];
+bool g_scratch_ready[kMaxDevices] = {false};
+std::string g_static_err;
+
+sgp_status static_fail(sgp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_static_err = buf;
+  g_create_err = buf;
+  return s;
+}
+
+// Device addresses of the scratch arrays for the current device (set-up on
+// the first call per device).
+sgp_status static_scratch(int device, StaticScratch** out) {
+  if (device < 0 || device >= kMaxDevices) return static_fail(SGP_EINVAL, "device %d out of range", device);
+  if (!g_scratch_ready[device]) {
+    StaticScratch sc;
+    cudaError_t e;
+    if ((e = cudaGetSymbolAddress((void**)&sc.partials, g_static_partials)) != cudaSuccess ||
+        (e = cudaGetSymbolAddress((void**)&sc.sums, g_static_sums)) != cudaSuccess ||
+        (e = cudaGetSymbolAddress(&sc.tw, g_static_tw)) != cudaSuccess)
+      return static_fail(SGP_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_scratch[device] = sc;
+    g_scratch_ready[device] = true;
+  }
+  *out = &g_scratch[device];
+  return SGP_OK;
+}
+
+template <typename R>
+sgp_status observables_static_impl(int dim, const int* nn, const double* LL, int batch,
+                                   const sgp_params* prm, double t, const void* field,
+                                   cudaStream_t stream, StaticScratch* sc, sgp_obs* out) {
+  int n[3] = {1, 1, 1};
+  double L[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+  for (int a = 0; a < dim; ++a) {
+    n[a] = nn[a];
+    L[a] = LL[a];
+    h[a] = 2.0 * L[a] / n[a];
+  }
+  const long long ntot = (long long)n[0] * n[1] * n[2];
+  const PassGeom gx = xpass_geom<R>(n[0]);
+  const int rows = n[1] * n[2];
+  const int nbx = (rows + gx.rows_or_tile - 1) / gx.rows_or_tile;
+  if ((size_t)nbx * OBX_NT * batch > kStaticMaxPartials)
+    return static_fail(SGP_EINVAL, "grid/batch needs %zu partial sums (limit %zu)",
+                       (size_t)nbx * OBX_NT * batch, kStaticMaxPartials);
+  for (int a = 1; a < dim; ++a) {
+    const PassGeom gl = linepass_geom<R>(n[a]);
+    const size_t tiles = (size_t)(n[0] + gl.rows_or_tile - 1) / gl.rows_or_tile;
+    const size_t planes = a == 1 ? n[2] : n[1];
+    if (tiles * planes * OBL_NT * batch > kStaticMaxPartials)
+      return static_fail(SGP_EINVAL, "grid/batch needs %zu partial sums (limit %zu)",
+                         tiles * planes * OBL_NT * batch, kStaticMaxPartials);
+  }
+  cudaError_t e;
+  // twiddles of every axis into the static table (TwE entries of 16 bytes)
+  TwE<R>* tw[3];
+  for (int a = 0; a < dim; ++a) {
+    tw[a] = reinterpret_cast<TwE<R>*>(reinterpret_cast<char*>(sc->tw) + (size_t)a * kStaticMaxN * 16);
+    if (sizeof(R) == 4)
+      k_twiddles_f32<<<(n[a] + 255) / 256, 256, 0, stream>>>(n[a], (TwE<float>*)tw[a]);
+    else
+      k_twiddles_f64<<<(n[a] + 255) / 256, 256, 0, stream>>>(n[a], (TwE<double>*)tw[a]);
+  }
+  // the reduction writes only the slots of the passes that run: start at zero
+  if ((e = cudaMemsetAsync(sc->sums, 0, sizeof(double) * (size_t)batch * OB_NT, stream)) != cudaSuccess)
+    return static_fail(SGP_ECUDA, "clear sums: %s", cudaGetErrorString(e));
+  ObsXArgs<R> ax{};
+  ax.ntot = ntot;
+  ax.rows = rows;
+  ax.ny = n[1];
+  ax.x0 = -L[0];
+  ax.hx = h[0];
+  ax.y0 = -L[1];
+  ax.hy = h[1];
+  ax.z0 = dim == 3 ? -L[2] : 0.0;
+  ax.hz = dim == 3 ? h[2] : 0.0;
+  ax.omega = prm->omega;
+  ax.t = t;
+  ax.c0 = prm->c0;
+  ax.c1 = prm->c1;
+  ax.c2 = prm->c2;
+  ax.gx2h = 0.5 * prm->gx * prm->gx;
+  ax.gy2h = 0.5 * prm->gy * prm->gy;
+  ax.gz2h = dim == 3 ? 0.5 * prm->gz * prm->gz : 0.0;
+  ax.partials = sc->partials;
+  ax.nblocks = nbx;
+  ax.field = (const cplx<R>*)field;
+  ax.tw = tw[0];
+  ax.dnu = (R)(kPi / L[0] / n[0]);
+  ax.NX = n[0];
+  if ((e = launch_obs_x<R>(n[0], ax, batch, stream)) != cudaSuccess)
+    return static_fail(SGP_ECUDA, "obs_x: %s", cudaGetErrorString(e));
+  k_reduce_partials<<<(batch * OBX_NT + 127) / 128, 128, 0, stream>>>(
+      sc->partials, nbx, OBX_NT, batch, sc->sums, OB_NT, 0);
+  for (int axis = 1; axis < dim; ++axis) {
+    const int NL = n[axis];
+    const PassGeom gl = linepass_geom<R>(NL);
+    ObsLArgs<R> al{};
+    static_cast<ObsArgsBase&>(al) = static_cast<const ObsArgsBase&>(ax);
+    al.field = (const cplx<R>*)field;
+    al.tw = tw[axis];
+    al.nx = n[0];
+    const long long nxy = (long long)n[0] * n[1];
+    int planes;
+    if (axis == 1) {
+      al.line_stride = n[0];
+      al.plane_stride = nxy;
+      planes = n[2];
+    } else {
+      al.line_stride = nxy;
+      al.plane_stride = n[0];
+      planes = n[1];
+    }
+    al.axis = axis;
+    al.dnu = (R)(kPi / L[axis] / NL);
+    al.NL = NL;
+    al.nblocks = ((n[0] + gl.rows_or_tile - 1) / gl.rows_or_tile) * planes;
+    if ((e = launch_obs_line<R>(NL, al, planes, batch, stream)) != cudaSuccess)
+      return static_fail(SGP_ECUDA, "obs_line: %s", cudaGetErrorString(e));
+    k_reduce_partials<<<(batch * OBL_NT + 127) / 128, 128, 0, stream>>>(
+        sc->partials, al.nblocks, OBL_NT, batch, sc->sums, OB_NT, axis == 1 ? OB_KY : OB_KZ);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return static_fail(SGP_ECUDA, "launch: %s", cudaGetErrorString(e));
+  double hsum[kStaticMaxBatch * OB_NT];   // host staging on the stack, no heap
+  if ((e = cudaMemcpyAsync(hsum, sc->sums, sizeof(double) * (size_t)batch * OB_NT,
+                           cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+    return static_fail(SGP_ECUDA, "read sums: %s", cudaGetErrorString(e));
+  const double cell = h[0] * h[1] * (dim == 3 ? h[2] : 1.0);
+  bool finite = true;
+  for (int m = 0; m < batch; ++m) {
+    const double* s = &hsum[(size_t)m * OB_NT];
+    sgp_obs o{};
+    o.t = t;
+    for (int k = 0; k < 5; ++k) {
+      o.comp_mass[k] = cell * s[OB_M0 + k];
+      o.mass += o.comp_mass[k];
+      o.magnetization += (2 - k) * o.comp_mass[k];
+    }
+    o.width2[0] = cell * s[OB_WX];
+    o.width2[1] = cell * s[OB_WY];
+    o.width2[2] = cell * s[OB_WZ];
+    o.e_kin = cell * (s[OB_KX] + s[OB_KY] + (dim == 3 ? s[OB_KZ] : 0.0));
+    o.e_pot = cell * s[OB_POT];
+    o.lz = cell * (s[OB_LZX] + s[OB_LZY]);
+    o.e_rot = -prm->omega * o.lz;
+    o.e_int = cell * s[OB_INT];
+    o.e_soc = -prm->gamma * cell * (s[OB_SOCX] + s[OB_SOCY]);
+    o.energy = o.e_kin + o.e_pot + o.e_rot + o.e_int + o.e_soc;
+    if (!std::isfinite(o.mass) || !std::isfinite(o.energy)) finite = false;
+    out[m] = o;
+  }
+  if (!finite) return static_fail(SGP_ENONFINITE, "non-finite observable");
+  return SGP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+sgp_status sgp_observables_static(int dim, const int* n, const double* L, int batch, int prec,
+                                  const sgp_params* p, double t, const void* field_dev,
+                                  int device, void* stream, sgp_obs* out) {
+  g_create_err.clear();
+  if (!n || !L || !p || !field_dev || !out) return static_fail(SGP_EINVAL, "NULL argument");
+  if (dim != 2 && dim != 3) return static_fail(SGP_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+  if (prec != SGP_F32 && prec != SGP_F64) return static_fail(SGP_EINVAL, "prec must be SGP_F32 or SGP_F64");
+  if (batch < 1 || batch > kStaticMaxBatch)
+    return static_fail(SGP_EINVAL, "batch must be in [1, %d] (got %d)", kStaticMaxBatch, batch);
+  for (int a = 0; a < dim; ++a) {
+    if (!supported_n(n[a]) || n[a] > kStaticMaxN)
+      return static_fail(SGP_EINVAL, "n[%d] = %d not supported", a, n[a]);
+    if (!(L[a] > 0.0) || !std::isfinite(L[a]))
+      return static_fail(SGP_EINVAL, "L[%d] must be positive and finite", a);
+  }
+  if (!finite_params(p) || !std::isfinite(t)) return static_fail(SGP_EINVAL, "non-finite parameter or time");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return static_fail(SGP_EINVAL, "CUDA device %d not available", device);
+  DeviceGuard guard(device);
+  StaticScratch* sc = nullptr;
+  sgp_status st = static_scratch(device, &sc);
+  if (st != SGP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return prec == SGP_F32 ? observables_static_impl<float>(dim, n, L, batch, p, t, field_dev, s, sc, out)
+                         : observables_static_impl<double>(dim, n, L, batch, p, t, field_dev, s, sc, out);
+}
+
+}  // extern "C"

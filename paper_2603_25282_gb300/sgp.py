@@ -82,6 +82,8 @@ def lib():
         "sgp_synchronize": (I, [P]),
         "sgp_launch_count": (LL, [P]),
         "sgp_destroy": (I, [P]),
+        "sgp_observables_static": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                       I, I, ctypes.POINTER(Params), D, P, I, P, ctypes.POINTER(Obs)]),
         "sgp_set_profiling": (I, [P, I]),
         "sgp_get_profile": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -176,6 +178,26 @@ def substep(ctx, kind, delta):
 def observables(ctx, batch=1):
     arr = (Obs * batch)()
     _check(lib().sgp_observables(ctx, arr), ctx)
+    return [o.as_dict() for o in arr]
+
+
+def observables_static(n, L, field_dev_ptr, batch=1, prec="f32", t=0.0, device=0,
+                       stream=None, **params):
+    """sgp_observables_static: observables of a device field the caller holds
+    (pointer as an int), computed without any allocation by the library."""
+    dim = len(n)
+    if np.isscalar(L):
+        L = [float(L)] * dim
+    m = max(3, dim)
+    na = (ctypes.c_int * m)(*(list(n) + [1] * (m - dim)))
+    La = (ctypes.c_double * m)(*(list(L) + [1.0] * (m - len(L))))
+    p = Params(**{k: float(params.get(k, 1.0 if k in ("gx", "gy", "gz") else 0.0))
+                  for k, _ in Params._fields_})
+    arr = (Obs * batch)()
+    st = lib().sgp_observables_static(dim, na, La, int(batch), PRECS[prec] if isinstance(prec, str) else prec,
+                                      ctypes.byref(p), float(t), ctypes.c_void_p(int(field_dev_ptr)),
+                                      int(device), ctypes.c_void_p(stream or 0), arr)
+    _check(st, None)
     return [o.as_dict() for o in arr]
 
 
