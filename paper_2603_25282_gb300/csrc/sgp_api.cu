@@ -62,21 +62,49 @@ __device__ inline void store_pair_w(double tx, double ty, double, double* ox, do
   *oy = ty;
 }
 
-// W_N^k = exp(-2 pi i k / N), k < N, as hi + lo in FP32 (see TwE).
-__global__ void k_twiddles_f32(int N, TwE<float>* out) {
+// Stage-ordered twiddle table of a length-N line with E elements per thread
+// (layout of tw_offset in sgp_fft.cuh): entry (s, r, j) = W_{NS*RD}^{j r},
+// evaluated in FP64; FP32 entries are stored as hi + lo (see TwE).
+__device__ inline void tw_angle(int N, int E, int k, double* s_out, double* c_out, bool* used) {
+  int off = 0, ns = radix_at(N, E, 0), st = 1;
+  *used = false;
+  while (true) {
+    const int rd = radix_at(N, E, st);
+    if (rd <= 0) return;
+    const int cnt = (rd - 1) * ns;
+    if (k < off + cnt) {
+      const int local = k - off;
+      const int r = local / ns + 1, j = local - (r - 1) * ns;
+      sincospi(-2.0 * (double)(j * r) / (double)(ns * rd), s_out, c_out);
+      *used = true;
+      return;
+    }
+    off += cnt;
+    ns *= rd;
+    ++st;
+  }
+}
+__global__ void k_twiddles_f32(int N, int E, TwE<float>* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
-  double s, c;
-  sincospi(-2.0 * (double)k / (double)N, &s, &c);
+  double s = 0.0, c = 1.0;
+  bool used;
+  tw_angle(N, E, k, &s, &c, &used);
   const float hx = (float)c, hy = (float)s;
   out[k] = TwE<float>{make_float2(hx, hy), make_float2((float)(c - hx), (float)(s - hy))};
 }
-__global__ void k_twiddles_f64(int N, TwE<double>* out) {
+__global__ void k_twiddles_f64(int N, int E, TwE<double>* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
-  double s, c;
-  sincospi(-2.0 * (double)k / (double)N, &s, &c);
+  double s = 0.0, c = 1.0;
+  bool used;
+  tw_angle(N, E, k, &s, &c, &used);
   out[k] = TwE<double>{make_double2(c, s)};
+}
+
+// Elements per thread of the line kernels (elems_per_thread<R, N>).
+inline int elems_for(int N, int prec) {
+  return (N % 3 == 0) ? 6 : (prec == SGP_F32 ? 8 : 4);
 }
 
 // Per-mode table of the linear flow over delta (Sec. 3.1, Eq. (sl1)), one
@@ -643,10 +671,11 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
   for (int a = 0; a < dim; ++a) {
     if ((e = cudaMalloc(&c->tw[a], (size_t)c->n[a] * 16)) != cudaSuccess)
       return bail(SGP_ENOMEM, "twiddle allocation", e);
+    const int E = elems_for(c->n[a], prec);
     if (prec == SGP_F32)
-      k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (TwE<float>*)c->tw[a]);
+      k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], E, (TwE<float>*)c->tw[a]);
     else
-      k_twiddles_f64<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], (TwE<double>*)c->tw[a]);
+      k_twiddles_f64<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], E, (TwE<double>*)c->tw[a]);
     c->launches++;
   }
   if ((e = cudaMalloc(&c->t_dev, sizeof(double))) != cudaSuccess)
@@ -897,10 +926,11 @@ sgp_status observables_static_impl(int dim, const int* nn, const double* LL, int
   TwE<R>* tw[3];
   for (int a = 0; a < dim; ++a) {
     tw[a] = reinterpret_cast<TwE<R>*>(reinterpret_cast<char*>(sc->tw) + (size_t)a * kStaticMaxN * 16);
+    const int E = elems_for(n[a], sizeof(R) == 4 ? SGP_F32 : SGP_F64);
     if (sizeof(R) == 4)
-      k_twiddles_f32<<<(n[a] + 255) / 256, 256, 0, stream>>>(n[a], (TwE<float>*)tw[a]);
+      k_twiddles_f32<<<(n[a] + 255) / 256, 256, 0, stream>>>(n[a], E, (TwE<float>*)tw[a]);
     else
-      k_twiddles_f64<<<(n[a] + 255) / 256, 256, 0, stream>>>(n[a], (TwE<double>*)tw[a]);
+      k_twiddles_f64<<<(n[a] + 255) / 256, 256, 0, stream>>>(n[a], E, (TwE<double>*)tw[a]);
   }
   // the reduction writes only the slots of the passes that run: start at zero
   if ((e = cudaMemsetAsync(sc->sums, 0, sizeof(double) * (size_t)batch * OB_NT, stream)) != cudaSuccess)

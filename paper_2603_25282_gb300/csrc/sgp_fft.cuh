@@ -107,6 +107,22 @@ __host__ __device__ constexpr int num_stages(int N, int E) {
   return s;
 }
 
+// Twiddle table layout: stage by stage (stages s >= 1, the first has none),
+// inside a stage r-major: entry (s, r, j) = W_{NS*RD}^{j r} = exp(-2 pi i j r
+// / (NS RD)) at tw_offset(N, E, s) + (r - 1) * NS + j, j < NS, 1 <= r < RD.
+// Butterflies of one warp read consecutive j for a fixed r, so the lookups
+// do not collide in the shared-memory banks.  The table has N - RD_0 < N
+// entries (sum over stages of NS (RD - 1) telescopes to N - RD_0).
+__host__ __device__ constexpr int tw_offset(int N, int E, int s) {
+  int off = 0, ns = 1;
+  for (int k = 0; k < s; ++k) {
+    const int rd = radix_at(N, E, k);
+    if (k >= 1) off += (rd - 1) * ns;
+    ns *= rd;
+  }
+  return off;
+}
+
 // Shared-memory padding: one element every 128 bytes breaks the power-of-two
 // strides of the early stages across banks.
 template <typename R> struct PadShift;
@@ -272,7 +288,7 @@ struct FftStages {
       constexpr int T = N / E;
       constexpr int B = E / RD;
       constexpr bool LAST = (NS * RD == N);
-      constexpr int TSTEP = N / (NS * RD);
+      constexpr int TOFF = tw_offset(N, E, S);
       TwE<R> w[B][RD];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
@@ -280,7 +296,7 @@ struct FftStages {
           const int j = (i + T * k) % NS;
 #pragma unroll
           for (int r = 1; r < RD; ++r) {
-            const TwE<R> t = tw[j * r * TSTEP];
+            const TwE<R> t = tw[TOFF + (r - 1) * NS + j];
             w[k][r] = DIR < 0 ? t : tw_conj(t);
           }
         }
@@ -339,14 +355,14 @@ struct FftStagesAdj {
       constexpr int T = N / E;
       constexpr int B = E / RD;
       constexpr bool LAST = (NS * RD == N);
-      constexpr int TSTEP = N / (NS * RD);
+      constexpr int TOFF = tw_offset(N, E, S);
       TwE<R> w[B][RD];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         if constexpr (NS > 1) {
           const int j = (i + T * k) % NS;
 #pragma unroll
-          for (int r = 1; r < RD; ++r) w[k][r] = tw_conj(tw[j * r * TSTEP]);
+          for (int r = 1; r < RD; ++r) w[k][r] = tw_conj(tw[TOFF + (r - 1) * NS + j]);
         }
       }
 #pragma unroll

@@ -154,6 +154,32 @@ __device__ __forceinline__ void spin2_increment(const cplx<R> (&v)[5], cplx<R> a
 __device__ __forceinline__ float mulc2(float x, float hi, float lo) { return fmaf(x, hi, x * lo); }
 __device__ __forceinline__ double mulc2(double x, double hi, double lo) { return x * hi; }
 
+// sin and cos of a small angle.  For |a| < 0.6 the Taylor series to degree
+// 9 (sin) and 10 (cos) is used: the remainders are below |a|^11/11! and
+// |a|^12/12! (< 1e-10 relative at |a| = 0.6), far below FP32 rounding, and
+// sin keeps full relative accuracy for tiny a, which the increment forms
+// need.  Larger angles go to the library sincosf.
+__device__ __forceinline__ void sincos_small(float a, float* s, float* c) {
+  if (fabsf(a) < 0.6f) {
+    const float a2 = a * a;
+    float ps = fmaf(a2, 2.7557319e-6f, -1.9841270e-4f);   // 1/9!, -1/7!
+    ps = fmaf(a2, ps, 8.3333333e-3f);                      // 1/5!
+    ps = fmaf(a2, ps, -1.6666667e-1f);                     // -1/3!
+    *s = fmaf(a * a2, ps, a);
+    float pc = fmaf(a2, -2.7557319e-7f, 2.4801587e-5f);    // -1/10!, 1/8!
+    pc = fmaf(a2, pc, -1.3888889e-3f);                     // -1/6!
+    pc = fmaf(a2, pc, 4.1666667e-2f);                      // 1/4!
+    pc = fmaf(a2, pc, -0.5f);                              // -1/2!
+    *c = fmaf(a2, pc, 1.0f);
+  } else {
+    sincosf(a, s, c);
+  }
+}
+__device__ __forceinline__ void sincos_small(double a, double* s, double* c) { sincos(a, s, c); }
+// 1/a rounded to nearest (FP32) or IEEE division (FP64)
+__device__ __forceinline__ float rcp_r(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_r(double a) { return 1.0 / a; }
+
 __device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sincos(a, s, c); }
 // 1/sqrt(a): the hardware estimate plus one Newton step (about 0.5 ulp and
@@ -198,15 +224,19 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   // A00 = (2 p2 m2 - 2 p1 m1 + p0^2)/sqrt5
   C A00 = csub(cmul(v[0], v[4]), cmul(v[1], v[3]));
   A00 = cscale(cadd(cscale(A00, (R)2), cmul(v[2], v[2])), rs5);
-  // (1) singlet-pair rotation, as the increment db of
+  // (1) singlet-pair rotation, as the increment of
   //     b = cos(c2 S d) Psi + i sin(c2 S d)/S (rho/5 Psi - A00 A conj(Psi)),
-  //     cos - 1 = -2 sin^2(c2 S d / 2)
+  //     cos - 1 = -2 sin^2(c2 S d / 2), sin(c2 S d)/S = 2 sin cos (half angle) / S
   const R S2 = rho * rho * (R)0.04 - cabs2(A00) * (R)0.2;
-  const R S = S2 > (R)0 ? sqrt(S2) : (R)0;
+  R S = (R)0, rS = (R)0;
+  if (S2 > (R)0) {
+    rS = rsqrt_r(S2);
+    S = S2 * rS;
+  }
   R sh1, ch1;
-  sincos_r((R)0.5 * c2 * S * delta, &sh1, &ch1);
+  sincos_small((R)0.5 * c2 * S * delta, &sh1, &ch1);
   const R cm1 = (R)-2 * sh1 * sh1;
-  const R sinc = S > (R)0 ? (R)2 * sh1 * ch1 / S : c2 * delta;
+  const R sinc = S > (R)0 ? (R)2 * sh1 * ch1 * rS : c2 * delta;
   const R r5 = rho * (R)0.2;
   const C As = cscale(A00, rs5);
   C inc[5], b[5];
@@ -230,15 +260,17 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   const R Fp2 = cabs2(Fp);
   const R F2 = Fp2 + Fz * Fz;
   if (F2 > (R)0) {
-    const R Fn = sqrt(F2);
+    const R rFn = rsqrt_r(F2);
+    const R Fn = F2 * rFn;
     R sh, ch;
-    sincos_r((R)0.5 * c1 * delta * Fn, &sh, &ch);
-    const R q = sh / Fn;
+    sincos_small((R)0.5 * c1 * delta * Fn, &sh, &ch);
+    const R q = sh * rFn;
     const R qFz = q * Fz;
-    const R cp = sqrt(ch * ch + qFz * qFz);
-    const R cpm1 = -(q * q * Fp2) / ((R)1 + cp);
-    const R icp = (R)1 / cp;
-    const R cmc = ch > (R)0 ? -(qFz * qFz) / (ch + cp) : ch - cp;   // cos - cp
+    const R cp2 = ch * ch + qFz * qFz;
+    const R icp = rsqrt_r(cp2);
+    const R cp = cp2 * icp;
+    const R cpm1 = -(q * q * Fp2) * rcp_r((R)1 + cp);
+    const R cmc = ch > (R)0 ? -(qFz * qFz) * rcp_r(ch + cp) : ch - cp;   // cos - cp
     const C am1 = mkc(cmc * icp, -qFz * icp);
     R mag;
     const C bhat = unit_dir(mkc(-Fp.y, -Fp.x), mag);   // direction of -i conj(F+)
@@ -253,7 +285,7 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   }
   // (3) scalar phase exp(-i d (V + (c0 + c2/5) rho)) - 1 = (-2 sin^2(ph/2), -sin(ph))
   R sh3, ch3;
-  sincos_r((R)-0.5 * delta * (V + c0p * rho), &sh3, &ch3);
+  sincos_small((R)-0.5 * delta * (V + c0p * rho), &sh3, &ch3);
   const C pm1 = mkc((R)-2 * sh3 * sh3, (R)2 * sh3 * ch3);
 #pragma unroll
   for (int k = 0; k < 5; ++k) v[k] = cadd(v[k], cadd(inc[k], cmul(pm1, b[k])));
@@ -268,11 +300,20 @@ struct XCfg {
   static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
   static constexpr int THREADS = ROWS * T;
   static constexpr int LP = line_pad<R>(N);
-  static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * ROWS * LP);
+  static constexpr int XCH = 2 * ROWS * LP;     // exchange buffers (complex)
+  static constexpr int STG = ROWS * 5 * N;      // nonlinear staging (complex)
+  static constexpr int BUF = XCH > STG ? XCH : STG;
+  static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)BUF;
+  // two CTAs per SM when they fit in shared memory
+  static constexpr int MINB = (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
+// x-pass: rows of all five components.  The nonlinear flow runs on the rows
+// staged in shared memory between the two transforms, as a plain loop over
+// points: one copy of its code (the unrolled form did not fit the
+// instruction cache) and registers only for the point being processed.
 template <typename R, int N, int E>
-__global__ void __launch_bounds__(XCfg<R, N, E>::THREADS)
+__global__ void __launch_bounds__(XCfg<R, N, E>::THREADS, XCfg<R, N, E>::MINB)
 k_xpass(XPassArgs<R> a) {
   typedef cplx<R> C;
   typedef XCfg<R, N, E> Cfg;
@@ -304,24 +345,36 @@ k_xpass(XPassArgs<R> a) {
   C* b1 = xb + (Cfg::ROWS + g) * Cfg::LP;
   if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
   if (a.mode & XP_NL) {
-    __syncthreads();   // s_rot
-    const R co = s_rot[0], si = s_rot[1];
-    const int ky = row % a.ny;
-    const int kz = row / a.ny;
-    const R y = a.y0 + (R)ky * a.hy;
-    const R z = a.z0 + (R)kz * a.hz;
-    const R vz = a.gz2h * z * z;
+    C* stg = xb;                      // [ROWS][5][N], aliases the exchange buffers
+    __syncthreads();                  // exchange buffers free, s_rot visible
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const R x = a.x0 + (R)(i + T * e) * a.hx;
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) stg[(g * 5 + c) * N + i + T * e] = v[c][e];
+    __syncthreads();
+    const R co = s_rot[0], si = s_rot[1];
+#pragma unroll 1
+    for (int pnt = threadIdx.x; pnt < Cfg::ROWS * N; pnt += Cfg::THREADS) {
+      const int gg = pnt / N, j = pnt - gg * N;
+      const int rr = blockIdx.x * Cfg::ROWS + gg;
+      const int ky = rr % a.ny, kz = rr / a.ny;
+      const R x = a.x0 + (R)j * a.hx;
+      const R y = a.y0 + (R)ky * a.hy;
+      const R z = a.z0 + (R)kz * a.hz;
       const R xr = co * x + si * y;
       const R yr = co * y - si * x;
-      const R V = a.gx2h * xr * xr + a.gy2h * yr * yr + vz;
-      C p[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
+      const R V = a.gx2h * xr * xr + a.gy2h * yr * yr + a.gz2h * z * z;
+      C* pp = stg + gg * 5 * N + j;
+      C p[5] = {pp[0], pp[N], pp[2 * N], pp[3 * N], pp[4 * N]};
       nonlinear_point<R>(p, V, a.delta, a.c0p, a.c1, a.c2);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) v[c][e] = p[c];
+      for (int c = 0; c < 5; ++c) pp[c * N] = p[c];
     }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = stg[(g * 5 + c) * N + i + T * e];
   }
   if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
   if (valid) {
