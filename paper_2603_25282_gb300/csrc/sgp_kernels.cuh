@@ -237,17 +237,17 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   sincos_small((R)0.5 * c2 * S * delta, &sh1, &ch1);
   const R cm1 = (R)-2 * sh1 * sh1;
   const R sinc = S > (R)0 ? (R)2 * sh1 * ch1 * rS : c2 * delta;
-  const R r5 = rho * (R)0.2;
-  const C As = cscale(A00, rs5);
+  // increment = (cm1 + i sinc rho/5) Psi - (i sinc A00/sqrt5) (sqrt5 A conj(Psi)),
+  // sqrt5 A conj(Psi) = (conj m2, -conj m1, conj p0, -conj p1, conj p2)
+  const C al = mkc(cm1, sinc * rho * (R)0.2);
+  const C be = cmuli(cscale(A00, sinc * rs5));
   C inc[5], b[5];
   {
-    // A conj(Psi) = (conj m2, -conj m1, conj p0, -conj p1, conj p2)/sqrt5
     const C ac[5] = {cconj(v[4]), cneg(cconj(v[3])), cconj(v[2]),
                      cneg(cconj(v[1])), cconj(v[0])};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      C t = csub(cscale(v[k], r5), cmul(As, ac[k]));    // rho/5 Psi - A00 A conj(Psi)
-      inc[k] = cadd(cscale(v[k], cm1), cscale(cmuli(t), sinc));
+      inc[k] = csub(cmul(al, v[k]), cmul(be, ac[k]));
       b[k] = cadd(v[k], inc[k]);
     }
   }
@@ -388,15 +388,19 @@ k_xpass(XPassArgs<R> a) {
 // ----------------------------------------------------------------------------
 // line-pass kernel (strided lines, tile of TILE consecutive x positions)
 // ----------------------------------------------------------------------------
+// Line pass geometry: up to 512 threads per CTA and at least 8 (FP32) / 4
+// (FP64) columns per tile, i.e. 64 B contiguous per line element (32 B
+// segments measured slower: they split HBM bursts between CTAs).
 template <typename R, int N, int E>
 struct LCfg {
   static constexpr int T = N / E;
   static constexpr int TMAX = sizeof(R) == 4 ? 32 : 16;
-  static constexpr int TMIN = sizeof(R) == 4 ? 4 : 2;
+  static constexpr int TMIN = sizeof(R) == 4 ? 8 : 4;
   static constexpr int TILE = (512 / T) > TMAX ? TMAX : ((512 / T) < TMIN ? TMIN : (512 / T));
   static constexpr int THREADS = TILE * T;
   static constexpr int LP = line_pad<R>(N);
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * TILE * LP);
+  static constexpr int MINB = (THREADS <= 256 && 2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
 template <typename R> struct ModeEntry { R khr, khi, am1r, am1i, cm1, sp, bx, by; };
@@ -441,7 +445,7 @@ __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
 }
 
 template <typename R, int N, int E>
-__global__ void __launch_bounds__(LCfg<R, N, E>::THREADS)
+__global__ void __launch_bounds__(LCfg<R, N, E>::THREADS, LCfg<R, N, E>::MINB)
 k_linepass(LPassArgs<R> a) {
   typedef cplx<R> C;
   typedef LCfg<R, N, E> Cfg;
