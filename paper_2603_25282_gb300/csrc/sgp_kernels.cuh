@@ -388,14 +388,15 @@ k_xpass(XPassArgs<R> a) {
 // ----------------------------------------------------------------------------
 // line-pass kernel (strided lines, tile of TILE consecutive x positions)
 // ----------------------------------------------------------------------------
-// Line pass geometry: up to 512 threads per CTA and at least 8 (FP32) / 4
-// (FP64) columns per tile, i.e. 64 B contiguous per line element (32 B
-// segments measured slower: they split HBM bursts between CTAs).
+// Line pass geometry: up to 512 threads per CTA; 8 FP32 (4 FP64) columns
+// per tile at N = 512, i.e. 64 B contiguous per line element (a 256-thread,
+// 4-column variant measured slower: 32 B segments split HBM bursts between
+// CTAs).
 template <typename R, int N, int E>
 struct LCfg {
   static constexpr int T = N / E;
   static constexpr int TMAX = sizeof(R) == 4 ? 32 : 16;
-  static constexpr int TMIN = sizeof(R) == 4 ? 8 : 4;
+  static constexpr int TMIN = sizeof(R) == 4 ? 4 : 2;
   static constexpr int TILE = (512 / T) > TMAX ? TMAX : ((512 / T) < TMIN ? TMIN : (512 / T));
   static constexpr int THREADS = TILE * T;
   static constexpr int LP = line_pad<R>(N);
