@@ -217,14 +217,15 @@ def run_ours(args, rank, world, local_rank):
 
     from paper_2603_25282_gb300 import inputs, sgp
     from paper_2603_25282_gb300 import build as _build
+    from paper_2603_25282_gb300.replicas import Replicas
 
     _build.build()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     torch.cuda.set_device(local_rank)
-    stream = torch.cuda.current_stream()
+    rep = Replicas("nccl", device=f"cuda:{local_rank}")
+    # a dedicated stream: the library issues its work (and graph replays) on
+    # it, and the CUDA events below are recorded on the same stream
+    stream = torch.cuda.Stream(device=local_rank)
+    torch.cuda.set_stream(stream)
     wl = args.workload
     n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
     if args.batch:
@@ -234,23 +235,17 @@ def run_ours(args, rank, world, local_rank):
     ctx.set_params(**prm)
     cdt = np.complex64 if prec == "f32" else np.complex128
     tdt = torch.complex64 if prec == "f32" else torch.complex128
-    host = np.stack([inputs.gaussian_random_phase(n, L, seed=1000 * rank + m + 2, amp=0.01)
+    host = np.stack([inputs.gaussian_random_phase(n, L, seed=rep.member_seed(m), amp=0.01)
                      for m in range(batch)]).astype(cdt)
     dev_init = torch.from_numpy(host).to(f"cuda:{local_rank}")
     pts = math.prod(n)
     state_bytes = host.nbytes
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        rep.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local_rank}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = rep.max_over_ranks
 
     # ---- device-resident timing -------------------------------------------
     ctx.set_state(dev_init, 0.0)
@@ -269,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms)
     clocks = clk.summary()
-    value = world * batch * pts * args.steps / (ms * 1e-3)
+    value = rep.weak_throughput(batch * pts * args.steps, ms * 1e-3)
 
     # ---- per-kernel roofline (CUDA events around every launch) ------------
     ctx.set_profiling(True)
@@ -310,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.get_state(out_pinned)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * batch * pts * e2e_steps / e2e_s
+    e2e_value = rep.weak_throughput(batch * pts * e2e_steps, e2e_s)
 
     # ---- CPU baseline (rank 0, N = 1) --------------------------------------
     cpu = None
@@ -350,8 +345,7 @@ def run_ours(args, rank, world, local_rank):
         }
         print(json.dumps(line))
     ctx.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
     return 0
 
 

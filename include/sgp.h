@@ -28,9 +28,12 @@
  *   - Ownership: every pointer argument stays owned by the caller; the
  *     context owns its device buffers and frees them in sgp_destroy.
  *   - Streams: all device work of a context is issued on the CUDA stream
- *     given at creation (a cudaStream_t passed as void*; NULL = the legacy
- *     default stream).  Calls documented as asynchronous return before the
- *     GPU work completes.
+ *     given at creation (a cudaStream_t passed as void*).  With NULL the
+ *     context creates and owns a private non-blocking stream; device-pointer
+ *     copies in or out are then ordered only on that stream (call
+ *     sgp_synchronize before touching a device destination from another
+ *     stream, and have a device source ready before the call).  Calls
+ *     documented as asynchronous return before the GPU work completes.
  *   - Errors: every call returns an sgp_status; on failure the context keeps
  *     a message readable with sgp_last_error.  No call throws or aborts.
  *     A context is not thread-safe: one host thread at a time.
@@ -105,16 +108,22 @@ const char* sgp_status_string(sgp_status s);
  * device is the CUDA ordinal; stream a cudaStream_t (or NULL).
  * Allocates the field, the FFT twiddle tables and the observable scratch on
  * `device`.  Errors: SGP_EINVAL for dim not in {2,3}, unsupported N, L <= 0,
- * batch < 1 or a NULL out; SGP_ENOMEM/SGP_ECUDA on allocation failure (no
- * context is returned then).  Parameters default to all zero with unit trap
- * frequencies; the field to zero at t = 0. */
+ * batch outside [1, 65535] or a NULL out; SGP_ENOMEM/SGP_ECUDA on allocation
+ * failure (no context is returned then).  Parameters default to all zero
+ * with unit trap frequencies; the field to zero at t = 0. */
 sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch,
                            int prec, int device, void* stream, sgp_ctx** out);
 
-/* Set the physical parameters (Sec. 1).  All batch members share them.
- * Synchronous on the host; takes effect for work issued afterwards.
- * Errors: SGP_EINVAL for NULL or non-finite values. */
+/* Set the physical parameters (Sec. 1) of every batch member to *p.
+ * Synchronous on the host (waits for the context stream); takes effect for
+ * work issued afterwards.  Errors: SGP_EINVAL for NULL or non-finite values. */
 sgp_status sgp_set_params(sgp_ctx* ctx, const sgp_params* p);
+
+/* Per-member parameters: p[m] for member m, count == batch.  Members may
+ * differ in every parameter; when they differ in Omega or gamma the
+ * linear-flow tables are built per member.  Same synchronisation and errors
+ * as sgp_set_params, plus SGP_EINVAL for count != batch. */
+sgp_status sgp_set_params_batch(sgp_ctx* ctx, const sgp_params* p, int count);
 
 /* Copy a field into the context and set the time to t0.  `src` holds
  * batch*5*nz*ny*nx complex elements of the context precision in the layout
@@ -138,11 +147,17 @@ sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
  * composition (Sec. 3.3; TS2 is Algorithm 1).  Adjacent nonlinear substeps of
  * consecutive steps, taken at the same time, are merged into one exact
  * nonlinear flow (the flow property of Eq. (solution2)), so a call costs
- * nsteps linear and nsteps+1 nonlinear substeps for TS2.  The field is in
- * physical space on return.  Asynchronous on the context stream.
+ * nsteps linear and nsteps+1 nonlinear substeps for TS2.  Runs of 128 steps
+ * or more are issued as replays of a captured CUDA graph of 64 steps (one
+ * extra nonlinear pass per 64 steps, where the chunks meet); the time is
+ * kept on the device in FP64 and advanced inside the graph.  The field is
+ * in physical space on return.  Asynchronous on the context stream.
  * Errors: SGP_EINVAL for nsteps < 0, dt <= 0 or non-finite dt; SGP_ESTATE
  * before sgp_set_state; SGP_ECUDA if a launch fails. */
 sgp_status sgp_step(sgp_ctx* ctx, long long nsteps, double dt, int scheme);
+
+/* Enable (default) or disable graph replay in sgp_step. */
+sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
 
 /* Apply one substep of size delta (delta may be negative, Sec. 3.3 TS4):
  * SGP_SUB_NONLINEAR applies the exact flow (solution2) at the current time;
@@ -155,6 +170,39 @@ sgp_status sgp_substep(sgp_ctx* ctx, int kind, double delta);
  * filled) if any sum is NaN or Inf. */
 sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
 
+/* ---------------------------------------------------------------------
+ * Ensembles: independent runs on different grids advanced together.
+ * Members are grouped by grid; each group is one batched context.  A step
+ * of the ensemble issues every group's passes; runs of 64 steps or more
+ * replay one captured CUDA graph per 64 steps in which the groups are
+ * parallel branches.  All members share the time and the composition;
+ * each has its own parameters.
+ * ------------------------------------------------------------------- */
+typedef struct sgp_ens sgp_ens;
+
+/* count members; n[m*dim + a] and L[m*dim + a] are member m's grid.
+ * stream as in sgp_create_grid.  Errors as sgp_create_grid per member. */
+sgp_status sgp_ensemble_create(int dim, int count, const int* n, const double* L,
+                               int prec, int device, void* stream, sgp_ens** out);
+/* Number of grid groups. */
+int sgp_ensemble_groups(const sgp_ens* ens);
+/* p[0..count-1], one parameter set per member (synchronous). */
+sgp_status sgp_ensemble_set_params(sgp_ens* ens, const sgp_params* p);
+/* Copy member m's field (5*nz*ny*nx elements of its grid) in or out; layout
+ * and on_device as sgp_set_state/sgp_get_state.  All members share t0. */
+sgp_status sgp_ensemble_set_member_state(sgp_ens* ens, int member, const void* src,
+                                         int src_on_device, double t0);
+sgp_status sgp_ensemble_get_member_state(sgp_ens* ens, int member, void* dst,
+                                         int dst_on_device);
+/* Advance every member by nsteps steps (asynchronous). */
+sgp_status sgp_ensemble_step(sgp_ens* ens, long long nsteps, double dt, int scheme);
+/* Observables of every member into out[0..count-1] (synchronises). */
+sgp_status sgp_ensemble_observables(sgp_ens* ens, sgp_obs* out);
+sgp_status sgp_ensemble_synchronize(sgp_ens* ens);
+long long sgp_ensemble_launch_count(const sgp_ens* ens);
+const char* sgp_ensemble_last_error(const sgp_ens* ens);
+sgp_status sgp_ensemble_destroy(sgp_ens* ens);
+
 /* Allocation-free observables (no counterpart in the paper; a service of
  * this library).  Computes the same quantities as sgp_observables for a
  * field the caller already holds on the device, without a context and
@@ -165,7 +213,8 @@ sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
  * implicit device synchronisation is not acceptable, and code that only
  * holds a device pointer to a field produced elsewhere.
  *
- * All scratch (per-block partial sums, FFT twiddles, final sums) lives in
+ * All scratch (per-block partial sums, FFT twiddles, final sums, member
+ * parameters) lives in
  * file-scope device arrays of fixed size that every GPU which loads the
  * library keeps until the process exits.  Limits: each n[a] as in
  * sgp_create_grid (<= 1024), batch <= 64, and at most 2^19 per-block partial

@@ -1,11 +1,14 @@
-// sgp_api.cu -- the C ABI declared in include/sgp.h: context management,
-// per-substep tables, pass orchestration of TS2/TS4 and the observables.
+// sgp_api.cu -- the C ABI declared in include/sgp.h: contexts and ensembles,
+// per-substep tables, pass orchestration of TS2/TS4 (with CUDA-graph replay
+// of step chunks) and the observables.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -25,15 +28,16 @@ const double kA2 = (1.0 - kCbrt2) / (2.0 * (2.0 - kCbrt2));
 const double kB1 = 1.0 / (2.0 - kCbrt2);
 const double kB2 = -kCbrt2 / (2.0 - kCbrt2);
 
+// Steps per captured CUDA graph (sgp_step replays it and runs the rest).
+constexpr long long kGraphChunk = 64;
+
 // ----------------------------------------------------------------------------
 // table kernels (FP64 arithmetic, stored in the context precision)
 // ----------------------------------------------------------------------------
-// Rounding of an FP64 complex target to the working precision.  For FP32
-// the 5x5 neighbourhood (+-2 ulp per coordinate) of the rounded pair is
-// searched for the smallest ||z| - |target|| + wz |z - target| (relative).
-// Twiddles use wz = 0.02: the inverse transform applies conj(W) on the same
-// path as the forward W, so only |W| enters the round trip and a modulus
-// error would otherwise accumulate over the steps.
+// Rounding of an FP64 unit-direction pair to FP32: the 5x5 neighbourhood
+// (+-2 ulp per coordinate) of the rounded pair is searched for the smallest
+// ||z| - |target|| + wz |z - target|, so the stored direction is of unit
+// modulus to well below an ulp.
 __device__ inline void store_pair_w(double tx, double ty, double wz, float* ox, float* oy) {
   const double m = sqrt(tx * tx + ty * ty);
   float xs[5], ys[5];
@@ -65,9 +69,8 @@ __device__ inline void store_pair_w(double tx, double ty, double, double* ox, do
 // Stage-ordered twiddle table of a length-N line with E elements per thread
 // (layout of tw_offset in sgp_fft.cuh): entry (s, r, j) = W_{NS*RD}^{j r},
 // evaluated in FP64; FP32 entries are stored as hi + lo (see TwE).
-__device__ inline void tw_angle(int N, int E, int k, double* s_out, double* c_out, bool* used) {
+__device__ inline void tw_angle(int N, int E, int k, double* s_out, double* c_out) {
   int off = 0, ns = radix_at(N, E, 0), st = 1;
-  *used = false;
   while (true) {
     const int rd = radix_at(N, E, st);
     if (rd <= 0) return;
@@ -76,7 +79,6 @@ __device__ inline void tw_angle(int N, int E, int k, double* s_out, double* c_ou
       const int local = k - off;
       const int r = local / ns + 1, j = local - (r - 1) * ns;
       sincospi(-2.0 * (double)(j * r) / (double)(ns * rd), s_out, c_out);
-      *used = true;
       return;
     }
     off += cnt;
@@ -88,8 +90,7 @@ __global__ void k_twiddles_f32(int N, int E, TwE<float>* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   double s = 0.0, c = 1.0;
-  bool used;
-  tw_angle(N, E, k, &s, &c, &used);
+  tw_angle(N, E, k, &s, &c);
   const float hx = (float)c, hy = (float)s;
   out[k] = TwE<float>{make_float2(hx, hy), make_float2((float)(c - hx), (float)(s - hy))};
 }
@@ -97,8 +98,7 @@ __global__ void k_twiddles_f64(int N, int E, TwE<double>* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   double s = 0.0, c = 1.0;
-  bool used;
-  tw_angle(N, E, k, &s, &c, &used);
+  tw_angle(N, E, k, &s, &c);
   out[k] = TwE<double>{make_double2(c, s)};
 }
 
@@ -108,18 +108,22 @@ inline int elems_for(int N, int prec) {
 }
 
 // Per-mode table of the linear flow over delta (Sec. 3.1, Eq. (sl1)), one
-// entry per (|p|, |q|) in the layout MT_* of sgp_kernels.cuh.  The angles are
+// entry per (|p|, |q|) in the layout MT_* of sgp_kernels.cuh, one table per
+// member (blockIdx.y) with that member's Omega and gamma.  The angles are
 // formed and the exponentials evaluated in FP64, and the small quantities
 // exp(-i chi) - 1, ahat - 1, cp - 1 are written without cancellation:
 //   exp(-i chi) - 1 = (-2 sin^2(chi/2), -sin chi),
 //   U11 = c - i s Omega/lambda (c, s = cos, sin of delta lambda/2),
 //   cp - 1 = -s^2 gamma^2 |nu_perp|^2 / lambda^2 / (1 + cp),
 //   ahat - 1 = (c - cp - i s Omega/lambda)/cp,  c - cp = -s^2 Omega^2/lambda^2/(c + cp).
-// kz[r] = exp(-i nu_z^2 delta/2) - 1.
+// kz[r] = exp(-i nu_z^2 delta/2) - 1 (shared by all members).
 template <typename R>
-__global__ void k_linear_tables(double delta, double omega, double gamma, int NX, int NY,
-                                int NZ, double Lx, double Ly, double Lz, R* mt, cplx<R>* kz) {
+__global__ void k_linear_tables(double delta, const MemberPrm* mp, int NX, int NY, int NZ,
+                                double Lx, double Ly, double Lz, R* mt, long long mt_member,
+                                cplx<R>* kz) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  const double omega = mp[m].omega, gamma = mp[m].gamma;
   const int hq = NY / 2 + 1;
   const int nent = (NX / 2 + 1) * hq;
   if (id < nent) {
@@ -145,7 +149,7 @@ __global__ void k_linear_tables(double delta, double omega, double gamma, int NX
     const double chi = 0.5 * (nup * nup + nuq * nuq) * delta;
     double sh, ch;
     sincos(0.5 * chi, &sh, &ch);
-    R* e = mt + (size_t)MT_STRIDE * id;
+    R* e = mt + (size_t)m * mt_member + (size_t)MT_STRIDE * id;
     e[MT_KHR] = (R)(-2.0 * sh * sh);
     e[MT_KHI] = (R)(-2.0 * sh * ch);
     e[MT_AM1R] = (R)am1r;
@@ -159,7 +163,7 @@ __global__ void k_linear_tables(double delta, double omega, double gamma, int NX
       e[MT_BY] = (R)0;
     }
   }
-  if (id < NZ) {
+  if (m == 0 && id < NZ) {
     const int ks_ = id < NZ / 2 ? id : id - NZ;
     const double nu = kPi * ks_ / Lz;
     double sh, ch;
@@ -168,16 +172,36 @@ __global__ void k_linear_tables(double delta, double omega, double gamma, int NX
   }
 }
 
+// Device FP64 time: set before a run of steps, advanced inside it (so a
+// replayed graph advances it too).
 __global__ void k_set_time(double* t, double v) { *t = v; }
+__global__ void k_add_time(double* t, double v) { *t += v; }
 
-// ----------------------------------------------------------------------------
-// context
-// ----------------------------------------------------------------------------
 struct LinTables {
   double delta = 0.0;
-  void* mt = nullptr;    // per-mode table, MT_STRIDE values per (|p|, |q|)
+  void* mt = nullptr;    // per-mode tables, MT_STRIDE values per (|p|, |q|), per member
   void* kz = nullptr;    // z kinetic factors (NZ entries)
 };
+
+struct GraphEntry {
+  long long steps;
+  double dt;
+  int scheme;
+  cudaGraphExec_t exec;
+};
+
+MemberPrm member_prm(const sgp_params& p, int dim) {
+  MemberPrm m;
+  m.omega = p.omega;
+  m.gamma = p.gamma;
+  m.c0 = p.c0;
+  m.c1 = p.c1;
+  m.c2 = p.c2;
+  m.gx2h = 0.5 * p.gx * p.gx;
+  m.gy2h = 0.5 * p.gy * p.gy;
+  m.gz2h = dim == 3 ? 0.5 * p.gz * p.gz : 0.0;
+  return m;
+}
 
 }  // namespace
 
@@ -190,16 +214,20 @@ struct sgp_ctx {
   int prec = SGP_F32;
   int device = 0;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;
   long long ntot = 0;
   size_t elem = 8;
   void* field = nullptr;
   void* tw[3] = {nullptr, nullptr, nullptr};
   double* t_dev = nullptr;
   double t = 0.0;
-  sgp_params prm{};
-  bool have_params = false;
+  std::vector<sgp_params> prm;      // per member
+  MemberPrm* mp_dev = nullptr;      // per member, on the device
+  bool shared_lin = true;           // all members share Omega and gamma
   bool have_state = false;
-  std::vector<LinTables> tables;    // cache keyed by delta (params fixed)
+  std::vector<LinTables> tables;    // cache keyed by delta
+  std::vector<GraphEntry> graphs;   // captured step chunks
+  bool use_graphs = true;
   double* partials = nullptr;       // observables scratch
   size_t partials_len = 0;
   double* obs_dev = nullptr;        // [batch][OB_NT]
@@ -234,6 +262,12 @@ sgp_status fail(sgp_ctx* c, sgp_status s, const char* fmt, ...) {
     if (e_ != cudaSuccess)                                                               \
       return fail((ctx), SGP_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
                   __FILE__, __LINE__);                                                   \
+  } while (0)
+
+#define SGP_TRY(x)                   \
+  do {                               \
+    sgp_status s_ = (x);             \
+    if (s_ != SGP_OK) return s_;     \
   } while (0)
 
 enum { PK_X = 0, PK_Y = 1, PK_Z = 2, PK_TAB = 3, PK_OBS = 4, PK_OTHER = 5, PK_N = 6 };
@@ -288,12 +322,34 @@ bool finite_params(const sgp_params* p) {
   return true;
 }
 
+void free_graphs(sgp_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
 void free_tables(sgp_ctx* c) {
   for (auto& t : c->tables) {
     cudaFree(t.mt);
     cudaFree(t.kz);
   }
   c->tables.clear();
+}
+
+// Copies the per-member parameters to the device (synchronous) and drops the
+// tables and graphs that depend on them.
+sgp_status upload_params(sgp_ctx* c) {
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  free_graphs(c);
+  free_tables(c);
+  std::vector<MemberPrm> h(c->batch);
+  c->shared_lin = true;
+  for (int m = 0; m < c->batch; ++m) {
+    h[m] = member_prm(c->prm[m], c->dim);
+    if (c->prm[m].omega != c->prm[0].omega || c->prm[m].gamma != c->prm[0].gamma)
+      c->shared_lin = false;
+  }
+  SGP_CUDA(c, cudaMemcpy(c->mp_dev, h.data(), sizeof(MemberPrm) * h.size(), cudaMemcpyHostToDevice));
+  return SGP_OK;
 }
 
 template <typename R>
@@ -303,18 +359,25 @@ sgp_status get_tables(sgp_ctx* c, double delta, const LinTables** out) {
       *out = &t;
       return SGP_OK;
     }
-  if (c->tables.size() >= 8) free_tables(c);
+  if (c->tables.size() >= 8) {
+    free_graphs(c);      // captured graphs point at the tables
+    free_tables(c);
+  }
   LinTables t;
   t.delta = delta;
   const int NX = c->n[0], NY = c->n[1], NZ = c->n[2];
   const size_t nent = (size_t)(NX / 2 + 1) * (NY / 2 + 1);
-  SGP_CUDA(c, cudaMalloc(&t.mt, nent * MT_STRIDE * sizeof(R)));
+  const int ntab = c->shared_lin ? 1 : c->batch;
+  SGP_CUDA(c, cudaMalloc(&t.mt, nent * MT_STRIDE * sizeof(R) * ntab));
   SGP_CUDA(c, cudaMalloc(&t.kz, (size_t)NZ * sizeof(cplx<R>)));
   const int work = (int)std::max<size_t>(nent, (size_t)NZ);
-  ProfScope ps(c, PK_TAB);
-  k_linear_tables<R><<<(work + 255) / 256, 256, 0, c->stream>>>(
-      delta, c->prm.omega, c->prm.gamma, NX, NY, NZ, c->L[0], c->L[1], c->L[2], (R*)t.mt,
-      (cplx<R>*)t.kz);
+  {
+    ProfScope ps(c, PK_TAB);
+    dim3 grid((work + 255) / 256, ntab);
+    k_linear_tables<R><<<grid, 256, 0, c->stream>>>(delta, c->mp_dev, NX, NY, NZ, c->L[0],
+                                                    c->L[1], c->L[2], (R*)t.mt,
+                                                    (long long)(nent * MT_STRIDE), (cplx<R>*)t.kz);
+  }
   c->launches++;
   SGP_CUDA(c, cudaGetLastError());
   c->tables.push_back(t);
@@ -341,13 +404,7 @@ sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
   a.z0 = c->dim == 3 ? (R)-c->L[2] : (R)0;
   a.hz = c->dim == 3 ? (R)c->h[2] : (R)0;
   a.delta = (R)delta;
-  a.c0p = (R)(c->prm.c0 + c->prm.c2 / 5.0);
-  a.c1 = (R)c->prm.c1;
-  a.c2 = (R)c->prm.c2;
-  a.gx2h = (R)(0.5 * c->prm.gx * c->prm.gx);
-  a.gy2h = (R)(0.5 * c->prm.gy * c->prm.gy);
-  a.gz2h = c->dim == 3 ? (R)(0.5 * c->prm.gz * c->prm.gz) : (R)0;
-  a.omega = c->prm.omega;
+  a.mp = c->mp_dev;
   a.t_base = c->t_dev;
   a.t_off = t_off;
   c->launches++;
@@ -381,6 +438,7 @@ sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
   a.NY = c->n[1];
   if (t) {
     a.mt = (const R*)t->mt;
+    a.mt_member = c->shared_lin ? 0 : (long long)(c->n[0] / 2 + 1) * (c->n[1] / 2 + 1) * MT_STRIDE;
     a.kz = (const cplx<R>*)t->kz;
   }
   {
@@ -393,12 +451,6 @@ sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
   SGP_CUDA(c, launch_linepass<R>(c->n[axis], a, planes, c->batch, c->stream));
   return SGP_OK;
 }
-
-#define SGP_TRY(x)                   \
-  do {                               \
-    sgp_status s_ = (x);             \
-    if (s_ != SGP_OK) return s_;     \
-  } while (0)
 
 // Linear flow over delta between x-passes.  Entry: x-spectral (the x-pass
 // has done its forward transform).  Exit: x-spectral.
@@ -416,49 +468,115 @@ sgp_status linear_middle(sgp_ctx* c, double delta) {
   return SGP_OK;
 }
 
-// Run nsteps of the composition.  Adjacent nonlinear substeps at the same
-// time are merged (exact flow property), so the pass sequence is
-//   N  L  N  L ... L  N   (N as x-passes, L as the line passes).
+// substep pattern of one step, Sec. 3.3
+std::vector<std::pair<char, double>> scheme_seq(int scheme) {
+  if (scheme == SGP_TS2) return {{'N', 0.5}, {'L', 1.0}, {'N', 0.5}};
+  return {{'N', kA1}, {'L', kB1}, {'N', kA2}, {'L', kB2}, {'N', kA2}, {'L', kB1}, {'N', kA1}};
+}
+
+// Issue nsteps of the composition from the device time *t_dev and advance
+// it by nsteps*dt.  Adjacent nonlinear substeps at the same time are merged
+// (exact flow property), so the pass sequence is N L N L ... L N with the N
+// as x-passes and the L as line passes.  Physical space in and out.
 template <typename R>
-sgp_status run_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
-  // substep pattern of one step, Sec. 3.3
-  std::vector<std::pair<char, double>> seq;
-  if (scheme == SGP_TS2) {
-    seq = {{'N', 0.5}, {'L', 1.0}, {'N', 0.5}};
-  } else {
-    seq = {{'N', kA1}, {'L', kB1}, {'N', kA2}, {'L', kB2},
-           {'N', kA2}, {'L', kB1}, {'N', kA1}};
-  }
-  const double t0 = c->t;
-  c->launches++;
-  {
-    ProfScope ps(c, PK_OTHER);
-    k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, t0);
-  }
-  SGP_CUDA(c, cudaGetLastError());
-  // first nonlinear substep (physical in, x-spectral out)
+sgp_status emit_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
+  const auto seq = scheme_seq(scheme);
   SGP_TRY(x_pass<R>(c, XP_NL | XP_FWD, seq[0].second * dt, 0.0));
   const int inner = (int)seq.size();
   for (long long s = 0; s < nsteps; ++s) {
-    double toff = (double)s * dt;      // offset of this step's start from t0
-    double sub = 0.0;                  // time advanced within the step
+    const double toff = (double)s * dt;   // offset of this step's start
+    double sub = 0.0;                     // time advanced within the step
     for (int k = 1; k < inner; ++k) {
       if (seq[k].first == 'L') {
-        const double d = seq[k].second * dt;
-        SGP_TRY(linear_middle<R>(c, d));
+        SGP_TRY(linear_middle<R>(c, seq[k].second * dt));
         sub += seq[k].second;
       } else {
         double coef = seq[k].second;
         const bool last_in_step = (k == inner - 1);
         const bool last = last_in_step && (s == nsteps - 1);
-        if (last_in_step && !last) coef += seq[0].second;   // merge with next step's first N
+        if (last_in_step && !last) coef += seq[0].second;   // merge with the next step's first N
         const double tn = last_in_step ? (double)(s + 1) * dt : toff + sub * dt;
         const int mode = last ? (XP_INV | XP_NL) : (XP_INV | XP_NL | XP_FWD);
         SGP_TRY(x_pass<R>(c, mode, coef * dt, tn));
       }
     }
   }
-  c->t = t0 + (double)nsteps * dt;
+  c->launches++;
+  {
+    ProfScope ps(c, PK_OTHER);
+    k_add_time<<<1, 1, 0, c->stream>>>(c->t_dev, (double)nsteps * dt);
+  }
+  SGP_CUDA(c, cudaGetLastError());
+  return SGP_OK;
+}
+
+// Tables for every substep size of the scheme (before a capture).
+template <typename R>
+sgp_status ensure_tables(sgp_ctx* c, double dt, int scheme) {
+  for (auto& st : scheme_seq(scheme))
+    if (st.first == 'L') {
+      const LinTables* t = nullptr;
+      SGP_TRY(get_tables<R>(c, st.second * dt, &t));
+    }
+  return SGP_OK;
+}
+
+// Captured chunk of `steps` steps on the context stream (cached).
+template <typename R>
+sgp_status get_graph(sgp_ctx* c, long long steps, double dt, int scheme, cudaGraphExec_t* out) {
+  for (auto& g : c->graphs)
+    if (g.steps == steps && g.dt == dt && g.scheme == scheme) {
+      *out = g.exec;
+      return SGP_OK;
+    }
+  if (c->graphs.size() >= 8) free_graphs(c);
+  SGP_TRY(ensure_tables<R>(c, dt, scheme));
+  const long long launches0 = c->launches;
+  SGP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  sgp_status st = emit_steps<R>(c, steps, dt, scheme);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  c->launches = launches0;      // counted when replayed
+  if (st != SGP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, SGP_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c, SGP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  c->graphs.push_back({steps, dt, scheme, exec});
+  *out = exec;
+  return SGP_OK;
+}
+
+// Launches issued by one chunk of `steps` steps (for the launch counter).
+long long chunk_launches(const sgp_ctx* c, long long steps, int scheme) {
+  const long long lin = (scheme == SGP_TS2 ? 1 : 3) * steps;
+  const long long per_l = c->dim == 2 ? 1 : 3;
+  return lin * per_l + lin + 1 + 1;
+}
+
+template <typename R>
+sgp_status run_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
+  c->launches++;
+  {
+    ProfScope ps(c, PK_OTHER);
+    k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, c->t);
+  }
+  SGP_CUDA(c, cudaGetLastError());
+  long long done = 0;
+  if (c->use_graphs && !c->profiling && nsteps >= 2 * kGraphChunk) {
+    cudaGraphExec_t exec = nullptr;
+    SGP_TRY(get_graph<R>(c, kGraphChunk, dt, scheme, &exec));
+    const long long reps = nsteps / kGraphChunk;
+    for (long long r = 0; r < reps; ++r) SGP_CUDA(c, cudaGraphLaunch(exec, c->stream));
+    c->launches += reps * chunk_launches(c, kGraphChunk, scheme);
+    done = reps * kGraphChunk;
+  }
+  if (done < nsteps) SGP_TRY(emit_steps<R>(c, nsteps - done, dt, scheme));
+  c->t += (double)nsteps * dt;
   return SGP_OK;
 }
 
@@ -481,6 +599,34 @@ sgp_status substep(sgp_ctx* c, int kind, double delta) {
 // ----------------------------------------------------------------------------
 // observables
 // ----------------------------------------------------------------------------
+void assemble_obs(const double* s, int dim, double cell, double t, const sgp_params& p,
+                  sgp_obs* o) {
+  *o = sgp_obs{};
+  o->t = t;
+  for (int k = 0; k < 5; ++k) {
+    o->comp_mass[k] = cell * s[OB_M0 + k];
+    o->mass += o->comp_mass[k];
+    o->magnetization += (2 - k) * o->comp_mass[k];
+  }
+  o->width2[0] = cell * s[OB_WX];
+  o->width2[1] = cell * s[OB_WY];
+  o->width2[2] = cell * s[OB_WZ];
+  o->e_kin = cell * (s[OB_KX] + s[OB_KY] + (dim == 3 ? s[OB_KZ] : 0.0));
+  o->e_pot = cell * s[OB_POT];
+  o->lz = cell * (s[OB_LZX] + s[OB_LZY]);
+  o->e_rot = -p.omega * o->lz;
+  o->e_int = cell * s[OB_INT];
+  o->e_soc = -p.gamma * cell * (s[OB_SOCX] + s[OB_SOCY]);
+  o->energy = o->e_kin + o->e_pot + o->e_rot + o->e_int + o->e_soc;
+}
+
+bool obs_finite(const sgp_obs& o) {
+  const double chk[6] = {o.mass, o.energy, o.magnetization, o.lz, o.width2[0], o.width2[1]};
+  for (double v : chk)
+    if (!std::isfinite(v)) return false;
+  return true;
+}
+
 template <typename R>
 sgp_status observables(sgp_ctx* c, sgp_obs* out) {
   const int NX = c->n[0];
@@ -497,14 +643,8 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
   ax.hy = c->h[1];
   ax.z0 = c->dim == 3 ? -c->L[2] : 0.0;
   ax.hz = c->dim == 3 ? c->h[2] : 0.0;
-  ax.omega = c->prm.omega;
   ax.t = c->t;
-  ax.c0 = c->prm.c0;
-  ax.c1 = c->prm.c1;
-  ax.c2 = c->prm.c2;
-  ax.gx2h = 0.5 * c->prm.gx * c->prm.gx;
-  ax.gy2h = 0.5 * c->prm.gy * c->prm.gy;
-  ax.gz2h = c->dim == 3 ? 0.5 * c->prm.gz * c->prm.gz : 0.0;
+  ax.mp = c->mp_dev;
   ax.partials = c->partials;
   ax.nblocks = nbx;
   ax.field = (const cplx<R>*)c->field;
@@ -562,36 +702,27 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
   const double cell = c->h[0] * c->h[1] * (c->dim == 3 ? c->h[2] : 1.0);
   bool finite = true;
   for (int m = 0; m < c->batch; ++m) {
-    const double* s = &h[(size_t)m * OB_NT];
-    if (c->dim == 2) {
-      // OB_KZ slot is not written in 2D (the z-line pass does not run)
-    }
-    sgp_obs o{};
-    o.t = c->t;
-    o.mass = 0.0;
-    o.magnetization = 0.0;
-    for (int k = 0; k < 5; ++k) {
-      o.comp_mass[k] = cell * s[OB_M0 + k];
-      o.mass += o.comp_mass[k];
-      o.magnetization += (2 - k) * o.comp_mass[k];
-    }
-    o.width2[0] = cell * s[OB_WX];
-    o.width2[1] = cell * s[OB_WY];
-    o.width2[2] = cell * s[OB_WZ];
-    const double kz = c->dim == 3 ? s[OB_KZ] : 0.0;
-    o.e_kin = cell * (s[OB_KX] + s[OB_KY] + kz);
-    o.e_pot = cell * s[OB_POT];
-    o.lz = cell * (s[OB_LZX] + s[OB_LZY]);
-    o.e_rot = -c->prm.omega * o.lz;
-    o.e_int = cell * s[OB_INT];
-    o.e_soc = -c->prm.gamma * cell * (s[OB_SOCX] + s[OB_SOCY]);
-    o.energy = o.e_kin + o.e_pot + o.e_rot + o.e_int + o.e_soc;
-    const double chk[6] = {o.mass, o.energy, o.magnetization, o.lz, o.width2[0], o.width2[1]};
-    for (double v : chk)
-      if (!std::isfinite(v)) finite = false;
-    out[m] = o;
+    assemble_obs(&h[(size_t)m * OB_NT], c->dim, cell, c->t, c->prm[m], &out[m]);
+    finite = finite && obs_finite(out[m]);
   }
   if (!finite) return fail(c, SGP_ENONFINITE, "non-finite observable");
+  return SGP_OK;
+}
+
+sgp_status validate_grid(int dim, const int* n, const double* L, int batch, int prec) {
+  if (!n || !L) return fail(nullptr, SGP_EINVAL, "NULL argument");
+  if (dim != 2 && dim != 3) return fail(nullptr, SGP_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+  if (prec != SGP_F32 && prec != SGP_F64)
+    return fail(nullptr, SGP_EINVAL, "prec must be SGP_F32 or SGP_F64");
+  if (batch < 1 || batch > 65535)
+    return fail(nullptr, SGP_EINVAL, "batch must be in [1, 65535] (got %d)", batch);
+  for (int a = 0; a < dim; ++a) {
+    if (!supported_n(n[a]))
+      return fail(nullptr, SGP_EINVAL,
+                  "n[%d] = %d not supported (2^a 3^b in {16..1024}, b <= 1)", a, n[a]);
+    if (!(L[a] > 0.0) || !std::isfinite(L[a]))
+      return fail(nullptr, SGP_EINVAL, "L[%d] must be positive and finite", a);
+  }
   return SGP_OK;
 }
 
@@ -602,7 +733,7 @@ sgp_status observables(sgp_ctx* c, sgp_obs* out) {
 // ============================================================================
 extern "C" {
 
-int sgp_version(void) { return 100; }
+int sgp_version(void) { return 200; }
 
 const char* sgp_status_string(sgp_status s) {
   switch (s) {
@@ -622,23 +753,14 @@ const char* sgp_last_error(const sgp_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_err.c_str();
 }
 
+sgp_status sgp_destroy(sgp_ctx* c);
+
 sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, int prec,
                            int device, void* stream, sgp_ctx** out) {
   g_create_err.clear();
-  if (!out || !n || !L) return fail(nullptr, SGP_EINVAL, "NULL argument");
+  if (!out) return fail(nullptr, SGP_EINVAL, "NULL argument");
   *out = nullptr;
-  if (dim != 2 && dim != 3) return fail(nullptr, SGP_EINVAL, "dim must be 2 or 3 (got %d)", dim);
-  if (prec != SGP_F32 && prec != SGP_F64)
-    return fail(nullptr, SGP_EINVAL, "prec must be SGP_F32 or SGP_F64");
-  if (batch < 1 || batch > 65535)
-    return fail(nullptr, SGP_EINVAL, "batch must be in [1, 65535] (got %d)", batch);
-  for (int a = 0; a < dim; ++a) {
-    if (!supported_n(n[a]))
-      return fail(nullptr, SGP_EINVAL,
-                  "n[%d] = %d not supported (2^a 3^b in {16..1024}, b <= 1)", a, n[a]);
-    if (!(L[a] > 0.0) || !std::isfinite(L[a]))
-      return fail(nullptr, SGP_EINVAL, "L[%d] must be positive and finite", a);
-  }
+  SGP_TRY(validate_grid(dim, n, L, batch, prec));
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return fail(nullptr, SGP_EINVAL, "CUDA device %d not available", device);
@@ -653,16 +775,30 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
   c->batch = batch;
   c->prec = prec;
   c->device = device;
-  c->stream = (cudaStream_t)stream;
   c->ntot = (long long)c->n[0] * c->n[1] * c->n[2];
   c->elem = prec == SGP_F32 ? 8 : 16;
-  c->prm.gx = c->prm.gy = c->prm.gz = 1.0;
+  sgp_params defaults{};
+  defaults.gx = defaults.gy = defaults.gz = 1.0;
+  c->prm.assign(batch, defaults);
   auto bail = [&](sgp_status s, const char* what, cudaError_t e) {
     fail(nullptr, s, "%s: %s", what, cudaGetErrorString(e));
     sgp_destroy(c);
     return s;
   };
   cudaError_t e;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(SGP_ECUDA, "stream", e);
+    c->own_stream = true;
+  }
+  // kernel attributes now, so that no later capture has to set them
+  for (int a = 0; a < dim; ++a) {
+    e = prec == SGP_F32 ? (a == 0 ? prepare_xpass<float>(c->n[a]) : prepare_linepass<float>(c->n[a]))
+                        : (a == 0 ? prepare_xpass<double>(c->n[a]) : prepare_linepass<double>(c->n[a]));
+    if (e != cudaSuccess) return bail(SGP_ECUDA, "kernel attributes", e);
+  }
   const size_t fbytes = (size_t)batch * 5 * c->ntot * c->elem;
   if ((e = cudaMalloc(&c->field, fbytes)) != cudaSuccess)
     return bail(SGP_ENOMEM, "field allocation", e);
@@ -680,6 +816,8 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
   }
   if ((e = cudaMalloc(&c->t_dev, sizeof(double))) != cudaSuccess)
     return bail(SGP_ENOMEM, "time allocation", e);
+  if ((e = cudaMalloc(&c->mp_dev, sizeof(MemberPrm) * batch)) != cudaSuccess)
+    return bail(SGP_ENOMEM, "parameter allocation", e);
   // observables scratch: the largest per-kernel partial array
   const PassGeom gx = prec == SGP_F32 ? xpass_geom<float>(c->n[0]) : xpass_geom<double>(c->n[0]);
   size_t need = (size_t)((c->n[1] * c->n[2] + gx.rows_or_tile - 1) / gx.rows_or_tile) * OBX_NT;
@@ -699,6 +837,11 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
     return bail(SGP_ECUDA, "observables clear", e);
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(SGP_ECUDA, "table launch", e);
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(SGP_ECUDA, "create sync", e);
+  if (upload_params(c) != SGP_OK) {
+    fail(nullptr, SGP_ECUDA, "%s", c->err.c_str());
+    sgp_destroy(c);
+    return SGP_ECUDA;
+  }
   *out = c;
   return SGP_OK;
 }
@@ -708,12 +851,19 @@ sgp_status sgp_set_params(sgp_ctx* c, const sgp_params* p) {
   if (!p) return fail(c, SGP_EINVAL, "NULL params");
   if (!finite_params(p)) return fail(c, SGP_EINVAL, "non-finite parameter");
   DeviceGuard guard(c->device);
-  // tables depend on (Omega, gamma); they may still be in use by queued work
-  cudaStreamSynchronize(c->stream);
-  free_tables(c);
-  c->prm = *p;
-  c->have_params = true;
-  return SGP_OK;
+  c->prm.assign(c->batch, *p);
+  return upload_params(c);
+}
+
+sgp_status sgp_set_params_batch(sgp_ctx* c, const sgp_params* p, int count) {
+  if (!c) return SGP_EINVAL;
+  if (!p) return fail(c, SGP_EINVAL, "NULL params");
+  if (count != c->batch) return fail(c, SGP_EINVAL, "count %d != batch %d", count, c->batch);
+  for (int m = 0; m < count; ++m)
+    if (!finite_params(&p[m])) return fail(c, SGP_EINVAL, "non-finite parameter (member %d)", m);
+  DeviceGuard guard(c->device);
+  c->prm.assign(p, p + count);
+  return upload_params(c);
 }
 
 sgp_status sgp_set_state(sgp_ctx* c, const void* src, int src_on_device, double t0) {
@@ -759,6 +909,12 @@ sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   DeviceGuard guard(c->device);
   return c->prec == SGP_F32 ? run_steps<float>(c, nsteps, dt, scheme)
                             : run_steps<double>(c, nsteps, dt, scheme);
+}
+
+sgp_status sgp_set_graphs(sgp_ctx* c, int enable) {
+  if (!c) return SGP_EINVAL;
+  c->use_graphs = enable != 0;
+  return SGP_OK;
 }
 
 sgp_status sgp_substep(sgp_ctx* c, int kind, double delta) {
@@ -826,16 +982,349 @@ sgp_status sgp_get_profile(sgp_ctx* c, long long* launches, double* ms) {
 sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;
   DeviceGuard guard(c->device);
-  cudaStreamSynchronize(c->stream);
+  if (c->stream || c->own_stream) cudaStreamSynchronize(c->stream);
+  free_graphs(c);
   free_tables(c);
   cudaFree(c->field);
   for (void* t : c->tw) cudaFree(t);
   cudaFree(c->t_dev);
+  cudaFree(c->mp_dev);
   cudaFree(c->partials);
   cudaFree(c->obs_dev);
   recycle_events(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
+  return SGP_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// ensembles of independent runs with different grids (one graph per chunk)
+// ============================================================================
+struct sgp_ens {
+  int dim = 2;
+  int count = 0;
+  int prec = SGP_F32;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<sgp_ctx*> groups;            // one context per distinct grid
+  std::vector<cudaStream_t> gstreams;      // capture branches
+  std::vector<cudaEvent_t> join;           // one per group
+  cudaEvent_t fork = nullptr;
+  std::vector<int> member_group, member_index;
+  std::vector<GraphEntry> graphs;
+  double t = 0.0;
+  bool have_state = false;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+sgp_status efail(sgp_ens* e, sgp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (e)
+    e->err = buf;
+  else
+    g_create_err = buf;
+  return s;
+}
+
+void ens_free_graphs(sgp_ens* e) {
+  for (auto& g : e->graphs) cudaGraphExecDestroy(g.exec);
+  e->graphs.clear();
+}
+
+// Issue `steps` steps of every group: group g on stream s(g).
+template <typename R>
+sgp_status ens_emit(sgp_ens* e, long long steps, double dt, int scheme, bool branches) {
+  for (size_t g = 0; g < e->groups.size(); ++g) {
+    sgp_ctx* c = e->groups[g];
+    const cudaStream_t saved = c->stream;
+    c->stream = branches ? e->gstreams[g] : e->stream;
+    sgp_status st = emit_steps<R>(c, steps, dt, scheme);
+    c->stream = saved;
+    if (st != SGP_OK) return efail(e, st, "group %zu: %s", g, c->err.c_str());
+  }
+  return SGP_OK;
+}
+
+template <typename R>
+sgp_status ens_graph(sgp_ens* e, long long steps, double dt, int scheme, cudaGraphExec_t* out) {
+  for (auto& g : e->graphs)
+    if (g.steps == steps && g.dt == dt && g.scheme == scheme) {
+      *out = g.exec;
+      return SGP_OK;
+    }
+  if (e->graphs.size() >= 8) ens_free_graphs(e);
+  for (sgp_ctx* c : e->groups) {
+    const cudaStream_t saved = c->stream;
+    c->stream = e->stream;
+    sgp_status st = ensure_tables<R>(c, dt, scheme);
+    c->stream = saved;
+    if (st != SGP_OK) return efail(e, st, "%s", c->err.c_str());
+  }
+  std::vector<long long> l0;
+  for (sgp_ctx* c : e->groups) l0.push_back(c->launches);
+  cudaError_t ce = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "begin capture: %s", cudaGetErrorString(ce));
+  cudaEventRecord(e->fork, e->stream);
+  for (size_t g = 0; g < e->groups.size(); ++g) cudaStreamWaitEvent(e->gstreams[g], e->fork, 0);
+  sgp_status st = ens_emit<R>(e, steps, dt, scheme, true);
+  for (size_t g = 0; g < e->groups.size(); ++g) {
+    cudaEventRecord(e->join[g], e->gstreams[g]);
+    cudaStreamWaitEvent(e->stream, e->join[g], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  ce = cudaStreamEndCapture(e->stream, &graph);
+  for (size_t g = 0; g < e->groups.size(); ++g) e->groups[g]->launches = l0[g];
+  if (st != SGP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "end capture: %s", cudaGetErrorString(ce));
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+  e->graphs.push_back({steps, dt, scheme, exec});
+  *out = exec;
+  return SGP_OK;
+}
+
+template <typename R>
+sgp_status ens_run(sgp_ens* e, long long nsteps, double dt, int scheme) {
+  for (sgp_ctx* c : e->groups) {
+    k_set_time<<<1, 1, 0, e->stream>>>(c->t_dev, e->t);
+    e->launches++;
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "set time: %s", cudaGetErrorString(ce));
+  long long done = 0;
+  if (nsteps >= kGraphChunk) {
+    cudaGraphExec_t exec = nullptr;
+    SGP_TRY(ens_graph<R>(e, kGraphChunk, dt, scheme, &exec));
+    const long long reps = nsteps / kGraphChunk;
+    for (long long r = 0; r < reps; ++r) {
+      ce = cudaGraphLaunch(exec, e->stream);
+      if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+    }
+    for (sgp_ctx* c : e->groups) e->launches += reps * chunk_launches(c, kGraphChunk, scheme);
+    done = reps * kGraphChunk;
+  }
+  if (done < nsteps) {
+    long long l0 = 0;
+    for (sgp_ctx* c : e->groups) l0 += c->launches;
+    SGP_TRY(ens_emit<R>(e, nsteps - done, dt, scheme, false));
+    long long l1 = 0;
+    for (sgp_ctx* c : e->groups) l1 += c->launches;
+    e->launches += l1 - l0;
+  }
+  e->t += (double)nsteps * dt;
+  for (sgp_ctx* c : e->groups) c->t = e->t;
+  return SGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sgp_status sgp_ensemble_destroy(sgp_ens* e);
+
+sgp_status sgp_ensemble_create(int dim, int count, const int* n, const double* L, int prec,
+                               int device, void* stream, sgp_ens** out) {
+  g_create_err.clear();
+  if (!out || !n || !L) return efail(nullptr, SGP_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (count < 1) return efail(nullptr, SGP_EINVAL, "count must be >= 1");
+  for (int m = 0; m < count; ++m) {
+    sgp_status st = validate_grid(dim, n + (size_t)m * dim, L + (size_t)m * dim, 1, prec);
+    if (st != SGP_OK) return efail(nullptr, st, "member %d: %s", m, g_create_err.c_str());
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return efail(nullptr, SGP_EINVAL, "CUDA device %d not available", device);
+  DeviceGuard guard(device);
+  sgp_ens* e = new sgp_ens();
+  e->dim = dim;
+  e->count = count;
+  e->prec = prec;
+  e->device = device;
+  cudaError_t ce;
+  if (stream) {
+    e->stream = (cudaStream_t)stream;
+  } else {
+    if ((ce = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      sgp_ensemble_destroy(e);
+      return efail(nullptr, SGP_ECUDA, "stream: %s", cudaGetErrorString(ce));
+    }
+    e->own_stream = true;
+  }
+  // group members by grid (sizes and half-widths)
+  std::map<std::vector<double>, int> key2g;
+  std::vector<std::vector<int>> members;
+  e->member_group.resize(count);
+  e->member_index.resize(count);
+  for (int m = 0; m < count; ++m) {
+    std::vector<double> key;
+    for (int a = 0; a < dim; ++a) key.push_back(n[(size_t)m * dim + a]);
+    for (int a = 0; a < dim; ++a) key.push_back(L[(size_t)m * dim + a]);
+    auto it = key2g.find(key);
+    int g;
+    if (it == key2g.end()) {
+      g = (int)members.size();
+      key2g[key] = g;
+      members.push_back({});
+    } else {
+      g = it->second;
+    }
+    e->member_group[m] = g;
+    e->member_index[m] = (int)members[g].size();
+    members[g].push_back(m);
+  }
+  for (size_t g = 0; g < members.size(); ++g) {
+    const int m0 = members[g][0];
+    cudaStream_t gs = nullptr;
+    if ((ce = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking)) != cudaSuccess) {
+      sgp_ensemble_destroy(e);
+      return efail(nullptr, SGP_ECUDA, "stream: %s", cudaGetErrorString(ce));
+    }
+    e->gstreams.push_back(gs);
+    cudaEvent_t ev = nullptr;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    e->join.push_back(ev);
+    sgp_ctx* c = nullptr;
+    sgp_status st = sgp_create_grid(dim, n + (size_t)m0 * dim, L + (size_t)m0 * dim,
+                                    (int)members[g].size(), prec, device, e->stream, &c);
+    if (st != SGP_OK) {
+      std::string msg = g_create_err;
+      sgp_ensemble_destroy(e);
+      return efail(nullptr, st, "group %zu: %s", g, msg.c_str());
+    }
+    e->groups.push_back(c);
+  }
+  cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+  *out = e;
+  return SGP_OK;
+}
+
+int sgp_ensemble_groups(const sgp_ens* e) { return e ? (int)e->groups.size() : 0; }
+
+sgp_status sgp_ensemble_set_params(sgp_ens* e, const sgp_params* p) {
+  if (!e) return SGP_EINVAL;
+  if (!p) return efail(e, SGP_EINVAL, "NULL params");
+  DeviceGuard guard(e->device);
+  ens_free_graphs(e);
+  for (size_t g = 0; g < e->groups.size(); ++g) {
+    sgp_ctx* c = e->groups[g];
+    std::vector<sgp_params> sub(c->batch);
+    for (int m = 0; m < e->count; ++m)
+      if (e->member_group[m] == (int)g) sub[e->member_index[m]] = p[m];
+    sgp_status st = sgp_set_params_batch(c, sub.data(), c->batch);
+    if (st != SGP_OK) return efail(e, st, "%s", c->err.c_str());
+  }
+  return SGP_OK;
+}
+
+sgp_status sgp_ensemble_set_member_state(sgp_ens* e, int member, const void* src,
+                                         int src_on_device, double t0) {
+  if (!e) return SGP_EINVAL;
+  if (member < 0 || member >= e->count) return efail(e, SGP_EINVAL, "member %d out of range", member);
+  if (!src) return efail(e, SGP_EINVAL, "NULL src");
+  if (!std::isfinite(t0)) return efail(e, SGP_EINVAL, "non-finite t0");
+  if (e->have_state && t0 != e->t) return efail(e, SGP_EINVAL, "all members share the time");
+  DeviceGuard guard(e->device);
+  sgp_ctx* c = e->groups[e->member_group[member]];
+  const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+  char* dst = (char*)c->field + (size_t)e->member_index[member] * bytes;
+  cudaError_t ce = cudaMemcpyAsync(dst, src, bytes,
+                                   src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                   e->stream);
+  if (ce == cudaSuccess && !src_on_device) ce = cudaStreamSynchronize(e->stream);
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "copy: %s", cudaGetErrorString(ce));
+  e->t = t0;
+  for (sgp_ctx* g : e->groups) {
+    g->t = t0;
+    g->have_state = true;
+  }
+  e->have_state = true;
+  return SGP_OK;
+}
+
+sgp_status sgp_ensemble_get_member_state(sgp_ens* e, int member, void* dst, int dst_on_device) {
+  if (!e) return SGP_EINVAL;
+  if (member < 0 || member >= e->count) return efail(e, SGP_EINVAL, "member %d out of range", member);
+  if (!dst) return efail(e, SGP_EINVAL, "NULL dst");
+  DeviceGuard guard(e->device);
+  sgp_ctx* c = e->groups[e->member_group[member]];
+  const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+  const char* src = (const char*)c->field + (size_t)e->member_index[member] * bytes;
+  cudaError_t ce = cudaMemcpyAsync(dst, src, bytes,
+                                   dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   e->stream);
+  if (ce == cudaSuccess && !dst_on_device) ce = cudaStreamSynchronize(e->stream);
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "copy: %s", cudaGetErrorString(ce));
+  return SGP_OK;
+}
+
+sgp_status sgp_ensemble_step(sgp_ens* e, long long nsteps, double dt, int scheme) {
+  if (!e) return SGP_EINVAL;
+  if (nsteps < 0) return efail(e, SGP_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return efail(e, SGP_EINVAL, "dt must be positive and finite");
+  if (scheme != SGP_TS2 && scheme != SGP_TS4) return efail(e, SGP_EINVAL, "unknown scheme %d", scheme);
+  if (!e->have_state) return efail(e, SGP_ESTATE, "sgp_ensemble_step before any member state");
+  if (nsteps == 0) return SGP_OK;
+  DeviceGuard guard(e->device);
+  return e->prec == SGP_F32 ? ens_run<float>(e, nsteps, dt, scheme)
+                            : ens_run<double>(e, nsteps, dt, scheme);
+}
+
+sgp_status sgp_ensemble_observables(sgp_ens* e, sgp_obs* out) {
+  if (!e) return SGP_EINVAL;
+  if (!out) return efail(e, SGP_EINVAL, "NULL out");
+  if (!e->have_state) return efail(e, SGP_ESTATE, "no state");
+  DeviceGuard guard(e->device);
+  for (size_t g = 0; g < e->groups.size(); ++g) {
+    sgp_ctx* c = e->groups[g];
+    std::vector<sgp_obs> tmp(c->batch);
+    sgp_status st = sgp_observables(c, tmp.data());
+    if (st != SGP_OK && st != SGP_ENONFINITE) return efail(e, st, "%s", c->err.c_str());
+    for (int m = 0; m < e->count; ++m)
+      if (e->member_group[m] == (int)g) out[m] = tmp[e->member_index[m]];
+  }
+  return SGP_OK;
+}
+
+sgp_status sgp_ensemble_synchronize(sgp_ens* e) {
+  if (!e) return SGP_EINVAL;
+  DeviceGuard guard(e->device);
+  cudaError_t ce = cudaStreamSynchronize(e->stream);
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "%s", cudaGetErrorString(ce));
+  return SGP_OK;
+}
+
+long long sgp_ensemble_launch_count(const sgp_ens* e) { return e ? e->launches : 0; }
+
+const char* sgp_ensemble_last_error(const sgp_ens* e) { return e ? e->err.c_str() : g_create_err.c_str(); }
+
+sgp_status sgp_ensemble_destroy(sgp_ens* e) {
+  if (!e) return SGP_OK;
+  DeviceGuard guard(e->device);
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  ens_free_graphs(e);
+  for (sgp_ctx* c : e->groups) sgp_destroy(c);
+  for (cudaStream_t s : e->gstreams) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+  if (e->fork) cudaEventDestroy(e->fork);
+  if (e->own_stream) cudaStreamDestroy(e->stream);
+  delete e;
   return SGP_OK;
 }
 
@@ -855,16 +1344,17 @@ constexpr int kStaticMaxN = 1024;
 static __device__ __align__(256) double g_static_partials[kStaticMaxPartials];
 static __device__ __align__(256) double g_static_sums[kStaticMaxBatch * OB_NT];
 static __device__ __align__(256) double2 g_static_tw[3 * kStaticMaxN];   // TwE: 16 B each
+static __device__ __align__(256) MemberPrm g_static_prm[kStaticMaxBatch];
 
 struct StaticScratch {
   double* partials = nullptr;
   double* sums = nullptr;
   void* tw = nullptr;
+  MemberPrm* prm = nullptr;
 };
 constexpr int kMaxDevices = 64;
 StaticScratch g_scratch[kMaxDevices];
 bool g_scratch_ready[kMaxDevices] = {false};
-std::string g_static_err;
 
 sgp_status static_fail(sgp_status s, const char* fmt, ...) {
   char buf[512];
@@ -872,7 +1362,6 @@ sgp_status static_fail(sgp_status s, const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
-  g_static_err = buf;
   g_create_err = buf;
   return s;
 }
@@ -886,7 +1375,8 @@ sgp_status static_scratch(int device, StaticScratch** out) {
     cudaError_t e;
     if ((e = cudaGetSymbolAddress((void**)&sc.partials, g_static_partials)) != cudaSuccess ||
         (e = cudaGetSymbolAddress((void**)&sc.sums, g_static_sums)) != cudaSuccess ||
-        (e = cudaGetSymbolAddress(&sc.tw, g_static_tw)) != cudaSuccess)
+        (e = cudaGetSymbolAddress(&sc.tw, g_static_tw)) != cudaSuccess ||
+        (e = cudaGetSymbolAddress((void**)&sc.prm, g_static_prm)) != cudaSuccess)
       return static_fail(SGP_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     g_scratch[device] = sc;
     g_scratch_ready[device] = true;
@@ -922,6 +1412,17 @@ sgp_status observables_static_impl(int dim, const int* nn, const double* LL, int
                          tiles * planes * OBL_NT * batch, kStaticMaxPartials);
   }
   cudaError_t e;
+  for (int a = 0; a < dim; ++a) {
+    e = sizeof(R) == 4 ? (a == 0 ? prepare_xpass<float>(n[a]) : prepare_linepass<float>(n[a]))
+                       : (a == 0 ? prepare_xpass<double>(n[a]) : prepare_linepass<double>(n[a]));
+    if (e != cudaSuccess) return static_fail(SGP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  }
+  // parameters: one entry for every member, staged from the stack
+  MemberPrm hp[kStaticMaxBatch];
+  for (int m = 0; m < batch; ++m) hp[m] = member_prm(*prm, dim);
+  if ((e = cudaMemcpyAsync(sc->prm, hp, sizeof(MemberPrm) * batch, cudaMemcpyHostToDevice, stream)) !=
+      cudaSuccess)
+    return static_fail(SGP_ECUDA, "parameters: %s", cudaGetErrorString(e));
   // twiddles of every axis into the static table (TwE entries of 16 bytes)
   TwE<R>* tw[3];
   for (int a = 0; a < dim; ++a) {
@@ -945,14 +1446,8 @@ sgp_status observables_static_impl(int dim, const int* nn, const double* LL, int
   ax.hy = h[1];
   ax.z0 = dim == 3 ? -L[2] : 0.0;
   ax.hz = dim == 3 ? h[2] : 0.0;
-  ax.omega = prm->omega;
   ax.t = t;
-  ax.c0 = prm->c0;
-  ax.c1 = prm->c1;
-  ax.c2 = prm->c2;
-  ax.gx2h = 0.5 * prm->gx * prm->gx;
-  ax.gy2h = 0.5 * prm->gy * prm->gy;
-  ax.gz2h = dim == 3 ? 0.5 * prm->gz * prm->gz : 0.0;
+  ax.mp = sc->prm;
   ax.partials = sc->partials;
   ax.nblocks = nbx;
   ax.field = (const cplx<R>*)field;
@@ -1001,26 +1496,8 @@ sgp_status observables_static_impl(int dim, const int* nn, const double* LL, int
   const double cell = h[0] * h[1] * (dim == 3 ? h[2] : 1.0);
   bool finite = true;
   for (int m = 0; m < batch; ++m) {
-    const double* s = &hsum[(size_t)m * OB_NT];
-    sgp_obs o{};
-    o.t = t;
-    for (int k = 0; k < 5; ++k) {
-      o.comp_mass[k] = cell * s[OB_M0 + k];
-      o.mass += o.comp_mass[k];
-      o.magnetization += (2 - k) * o.comp_mass[k];
-    }
-    o.width2[0] = cell * s[OB_WX];
-    o.width2[1] = cell * s[OB_WY];
-    o.width2[2] = cell * s[OB_WZ];
-    o.e_kin = cell * (s[OB_KX] + s[OB_KY] + (dim == 3 ? s[OB_KZ] : 0.0));
-    o.e_pot = cell * s[OB_POT];
-    o.lz = cell * (s[OB_LZX] + s[OB_LZY]);
-    o.e_rot = -prm->omega * o.lz;
-    o.e_int = cell * s[OB_INT];
-    o.e_soc = -prm->gamma * cell * (s[OB_SOCX] + s[OB_SOCY]);
-    o.energy = o.e_kin + o.e_pot + o.e_rot + o.e_int + o.e_soc;
-    if (!std::isfinite(o.mass) || !std::isfinite(o.energy)) finite = false;
-    out[m] = o;
+    assemble_obs(&hsum[(size_t)m * OB_NT], dim, cell, t, *prm, &out[m]);
+    finite = finite && obs_finite(out[m]);
   }
   if (!finite) return static_fail(SGP_ENONFINITE, "non-finite observable");
   return SGP_OK;

@@ -47,15 +47,38 @@ PassGeom xpass_geom<Real>(int N) {
 }
 
 template <int N>
+static cudaError_t xpass_prepare_n() {
+  constexpr int E = elems_per_thread<Real, N>();
+  static int done = -1;
+  cudaError_t e = prepare(k_xpass<Real, N, E>, XCfg<Real, N, E>::SMEM, &done);
+  if (e != cudaSuccess) return e;
+  static int done_o = -1;
+  return prepare(k_obs_x<Real, N, E>, XCfg<Real, N, E>::SMEM, &done_o);
+}
+
+template <int N>
 static cudaError_t xpass_n(const XPassArgs<Real>& a, int members, cudaStream_t s) {
   constexpr int E = elems_per_thread<Real, N>();
   typedef XCfg<Real, N, E> Cfg;
-  static int done = -1;
-  cudaError_t e = prepare(k_xpass<Real, N, E>, Cfg::SMEM, &done);
+  cudaError_t e = xpass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.rows + Cfg::ROWS - 1) / Cfg::ROWS, members);
   k_xpass<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+
+template <>
+cudaError_t prepare_xpass<Real>(int N) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return xpass_prepare_n<NN>();
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 template <>
@@ -75,8 +98,7 @@ template <int N>
 static cudaError_t obs_x_n(const ObsXArgs<Real>& a, int members, cudaStream_t s) {
   constexpr int E = elems_per_thread<Real, N>();
   typedef XCfg<Real, N, E> Cfg;
-  static int done = -1;
-  cudaError_t e = prepare(k_obs_x<Real, N, E>, Cfg::SMEM, &done);
+  cudaError_t e = xpass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.rows + Cfg::ROWS - 1) / Cfg::ROWS, members);
   k_obs_x<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
@@ -114,16 +136,39 @@ PassGeom linepass_geom<Real>(int N) {
 }
 
 template <int N>
+static cudaError_t linepass_prepare_n() {
+  constexpr int E = elems_per_thread<Real, N>();
+  static int done = -1;
+  cudaError_t e = prepare(k_linepass<Real, N, E>, LCfg<Real, N, E>::SMEM, &done);
+  if (e != cudaSuccess) return e;
+  static int done_o = -1;
+  return prepare(k_obs_line<Real, N, E>, LCfg<Real, N, E>::SMEM, &done_o);
+}
+
+template <int N>
 static cudaError_t linepass_n(const LPassArgs<Real>& a, int planes, int members,
                               cudaStream_t s) {
   constexpr int E = elems_per_thread<Real, N>();
   typedef LCfg<Real, N, E> Cfg;
-  static int done = -1;
-  cudaError_t e = prepare(k_linepass<Real, N, E>, Cfg::SMEM, &done);
+  cudaError_t e = linepass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
   k_linepass<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+
+template <>
+cudaError_t prepare_linepass<Real>(int N) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return linepass_prepare_n<NN>();
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 template <>
@@ -145,8 +190,7 @@ static cudaError_t obs_line_n(const ObsLArgs<Real>& a, int planes, int members,
                               cudaStream_t s) {
   constexpr int E = elems_per_thread<Real, N>();
   typedef LCfg<Real, N, E> Cfg;
-  static int done = -1;
-  cudaError_t e = prepare(k_obs_line<Real, N, E>, Cfg::SMEM, &done);
+  cudaError_t e = linepass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
   k_obs_line<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);

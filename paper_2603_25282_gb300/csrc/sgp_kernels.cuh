@@ -26,6 +26,14 @@ namespace sgp {
 
 // x-pass mode bits
 enum { XP_INV = 1, XP_NL = 2, XP_FWD = 4 };
+
+// Physical parameters of one batch member (Sec. 1, Eq. (CGPEs) and the
+// harmonic trap), kept in FP64 on the device and read by every CTA of the
+// member.
+struct MemberPrm {
+  double omega, gamma, c0, c1, c2;
+  double gx2h, gy2h, gz2h;   // gx^2/2, gy^2/2, gz^2/2 (gz2h = 0 in 2D)
+};
 // line-pass mode bits
 enum { LP_FWD = 1, LP_MIX = 2, LP_INV = 4 };
 
@@ -39,8 +47,8 @@ struct XPassArgs {
   int mode;
   R x0, hx, y0, hy, z0, hz;      // coordinates x_j = x0 + j*hx
   // nonlinear flow over delta at time t = *t_base + t_off
-  R delta, c0p, c1, c2, gx2h, gy2h, gz2h;
-  double omega;
+  R delta;
+  const MemberPrm* mp;           // [batch]
   const double* t_base;
   double t_off;
 };
@@ -56,8 +64,11 @@ struct LPassArgs {
   int mode;
   int axis;                   // 1: lines along y (2D); 2: lines along z (3D)
   int NX, NY;                 // grid sizes along x and y (mode indices)
-  // per-mode table over (|p|, |q|), MT_STRIDE values per entry (see MT_*)
+  // per-mode table over (|p|, |q|), MT_STRIDE values per entry (see MT_*);
+  // member m uses mt + m * mt_member (mt_member = 0 when all members share
+  // Omega and gamma)
   const R* mt;
+  long long mt_member;
   const cplx<R>* kz;          // exp(-i nu_z^2 d/2) - 1 (3D only)
   R inv_hi, inv_lo;           // 1/(NX NY [NZ]) as an unevaluated sum hi + lo
 };
@@ -325,10 +336,11 @@ k_xpass(XPassArgs<R> a) {
   const int g = threadIdx.x / T;
   const int i = threadIdx.x - g * T;
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
+  const MemberPrm& P = a.mp[blockIdx.y];
   if ((a.mode & XP_NL) && threadIdx.x == 0) {
     const double t = *a.t_base + a.t_off;
     double sn, cs;
-    sincos(a.omega * t, &sn, &cs);
+    sincos(P.omega * t, &sn, &cs);
     s_rot[0] = (R)cs;
     s_rot[1] = (R)sn;
   }
@@ -353,6 +365,8 @@ k_xpass(XPassArgs<R> a) {
       for (int e = 0; e < E; ++e) stg[(g * 5 + c) * N + i + T * e] = v[c][e];
     __syncthreads();
     const R co = s_rot[0], si = s_rot[1];
+    const R c0p = (R)(P.c0 + P.c2 / 5.0), c1 = (R)P.c1, c2 = (R)P.c2;
+    const R gx2h = (R)P.gx2h, gy2h = (R)P.gy2h, gz2h = (R)P.gz2h;
 #pragma unroll 1
     for (int pnt = threadIdx.x; pnt < Cfg::ROWS * N; pnt += Cfg::THREADS) {
       const int gg = pnt / N, j = pnt - gg * N;
@@ -363,10 +377,10 @@ k_xpass(XPassArgs<R> a) {
       const R z = a.z0 + (R)kz * a.hz;
       const R xr = co * x + si * y;
       const R yr = co * y - si * x;
-      const R V = a.gx2h * xr * xr + a.gy2h * yr * yr + a.gz2h * z * z;
+      const R V = gx2h * xr * xr + gy2h * yr * yr + gz2h * z * z;
       C* pp = stg + gg * 5 * N + j;
       C p[5] = {pp[0], pp[N], pp[2 * N], pp[3 * N], pp[4 * N]};
-      nonlinear_point<R>(p, V, a.delta, a.c0p, a.c1, a.c2);
+      nonlinear_point<R>(p, V, a.delta, c0p, c1, c2);
 #pragma unroll
       for (int c = 0; c < 5; ++c) pp[c * N] = p[c];
     }
@@ -428,7 +442,7 @@ __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
   const int qs = q < a.NY / 2 ? q : q - a.NY;
   const int aps = ps < 0 ? -ps : ps;
   const int aqs = qs < 0 ? -qs : qs;
-  const ModeEntry<R> m = load_mode(a.mt, aps * (a.NY / 2 + 1) + aqs);
+  const ModeEntry<R> m = load_mode(a.mt + (size_t)blockIdx.z * a.mt_member, aps * (a.NY / 2 + 1) + aqs);
   const C bhat = mkc(ps < 0 ? -m.bx : m.bx, qs < 0 ? m.by : -m.by);
   C kh = mkc(m.khr, m.khi);
   if (a.axis == 2) {
@@ -513,8 +527,8 @@ struct ObsArgsBase {
   long long ntot;
   int rows, ny;
   double x0, hx, y0, hy, z0, hz;
-  double omega, t;
-  double c0, c1, c2, gx2h, gy2h, gz2h;
+  double t;
+  const MemberPrm* mp;   // [batch]
   double* partials;      // [member][nblocks][terms of the kernel]
   int nblocks;           // blocks per member
 };
@@ -604,7 +618,8 @@ k_obs_x(ObsXArgs<R> a) {
 #pragma unroll
   for (int k = 0; k < 13; ++k) acc[k] = 0.0;
   if (valid) {
-    const double co = cos(a.omega * a.t), si = sin(a.omega * a.t);
+    const MemberPrm& P = a.mp[blockIdx.y];
+    const double co = cos(P.omega * a.t), si = sin(P.omega * a.t);
     const int ky = row % a.ny, kz = row / a.ny;
     const double y = a.y0 + ky * a.hy, z = a.z0 + kz * a.hz;
     const double s6h = 1.22474487139158904910, s6 = 2.44948974278317809820;
@@ -631,7 +646,7 @@ k_obs_x(ObsXArgs<R> a) {
       acc[OB_WX] += xr * xr * rho;
       acc[OB_WY] += yr * yr * rho;
       acc[OB_WZ] += z * z * rho;
-      acc[OB_POT] += (a.gx2h * xr * xr + a.gy2h * yr * yr + a.gz2h * z * z) * rho;
+      acc[OB_POT] += (P.gx2h * xr * xr + P.gy2h * yr * yr + P.gz2h * z * z) * rho;
       const double Fz = 2.0 * (m[0] - m[4]) + m[1] - m[3];
       // F_+ = 2(conj(p2)p1 + conj(m1)m2) + sqrt6 (conj(p1)p0 + conj(p0)m1)
       const double fpr = 2.0 * (re[0] * re[1] + im[0] * im[1] + re[3] * re[4] + im[3] * im[4]) +
@@ -642,8 +657,8 @@ k_obs_x(ObsXArgs<R> a) {
                         re[2] * re[2] - im[2] * im[2];
       const double aI = 2.0 * (re[0] * im[4] + im[0] * re[4]) - 2.0 * (re[1] * im[3] + im[1] * re[3]) +
                         2.0 * re[2] * im[2];
-      acc[OB_INT] += 0.5 * a.c0 * rho * rho + 0.5 * a.c1 * (fpr * fpr + fpi * fpi + Fz * Fz) +
-                     0.5 * a.c2 * (aR * aR + aI * aI) * 0.2;
+      acc[OB_INT] += 0.5 * P.c0 * rho * rho + 0.5 * P.c1 * (fpr * fpr + fpi * fpi + Fz * Fz) +
+                     0.5 * P.c2 * (aR * aR + aI * aI) * 0.2;
       acc[OB_KX] += 0.5 * kin;
       acc[OB_LZX] += -y * lzi;
       // SOC, x part: sum_i coef_i Re[-conj(phi_i) d phi_{i+1} + conj(phi_{i+1}) d phi_i]

@@ -38,6 +38,11 @@ struct PassGeom {
 template <typename R> PassGeom xpass_geom(int N);
 template <typename R> PassGeom linepass_geom(int N);
 
+// Set the kernels' shared-memory attributes for line length N on the
+// current device (done before any stream capture).
+template <typename R> cudaError_t prepare_xpass(int N);
+template <typename R> cudaError_t prepare_linepass(int N);
+
 template <typename R>
 cudaError_t launch_xpass(int N, const XPassArgs<R>& a, int members, cudaStream_t s);
 template <typename R>

@@ -73,6 +73,20 @@ def lib():
         "sgp_create_grid": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 I, I, I, P, ctypes.POINTER(P)]),
         "sgp_set_params": (I, [P, ctypes.POINTER(Params)]),
+        "sgp_set_params_batch": (I, [P, ctypes.POINTER(Params), I]),
+        "sgp_set_graphs": (I, [P, I]),
+        "sgp_ensemble_create": (I, [I, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                    I, I, P, ctypes.POINTER(P)]),
+        "sgp_ensemble_groups": (I, [P]),
+        "sgp_ensemble_set_params": (I, [P, ctypes.POINTER(Params)]),
+        "sgp_ensemble_set_member_state": (I, [P, I, P, I, D]),
+        "sgp_ensemble_get_member_state": (I, [P, I, P, I]),
+        "sgp_ensemble_step": (I, [P, LL, D, I]),
+        "sgp_ensemble_observables": (I, [P, ctypes.POINTER(Obs)]),
+        "sgp_ensemble_synchronize": (I, [P]),
+        "sgp_ensemble_launch_count": (LL, [P]),
+        "sgp_ensemble_last_error": (ctypes.c_char_p, [P]),
+        "sgp_ensemble_destroy": (I, [P]),
         "sgp_set_state": (I, [P, P, I, D]),
         "sgp_get_state": (I, [P, P, I]),
         "sgp_get_time": (I, [P, ctypes.POINTER(ctypes.c_double)]),
@@ -142,10 +156,24 @@ def create_grid(n, L, batch=1, prec="f32", device=0, stream=None):
     return out
 
 
+def _params(kw):
+    return Params(**{k: float(kw.get(k, 1.0 if k in ("gx", "gy", "gz") else 0.0))
+                     for k, _ in Params._fields_})
+
+
 def set_params(ctx, **kw):
-    p = Params(**{k: float(kw.get(k, 1.0 if k in ("gx", "gy", "gz") else 0.0))
-                  for k, _ in Params._fields_})
+    p = _params(kw)
     _check(lib().sgp_set_params(ctx, ctypes.byref(p)), ctx)
+
+
+def set_params_batch(ctx, plist):
+    """Per-member parameters: plist is a list of dicts (one per member)."""
+    arr = (Params * len(plist))(*[_params(d) for d in plist])
+    _check(lib().sgp_set_params_batch(ctx, arr, len(plist)), ctx)
+
+
+def set_graphs(ctx, enable):
+    _check(lib().sgp_set_graphs(ctx, int(bool(enable))), ctx)
 
 
 def set_state(ctx, src, dtype, t0=0.0):
@@ -250,6 +278,12 @@ class Context:
     def set_params(self, **kw):
         set_params(self.handle, **kw)
 
+    def set_params_batch(self, plist):
+        set_params_batch(self.handle, plist)
+
+    def set_graphs(self, enable):
+        set_graphs(self.handle, enable)
+
     def set_state(self, src, t0=0.0):
         set_state(self.handle, src, self.dtype, t0)
 
@@ -287,6 +321,95 @@ class Context:
     def close(self):
         if self.handle:
             destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# ensembles of runs on different grids
+# ---------------------------------------------------------------------------
+def _echeck(status, ens):
+    if status != 0:
+        L = lib()
+        raise SgpError(L.sgp_status_string(status).decode(), L.sgp_ensemble_last_error(ens).decode())
+
+
+class Ensemble:
+    """sgp_ensemble_*: members on different grids, advanced together."""
+
+    def __init__(self, grids, prec="f32", device=0, stream=None):
+        """grids: list of (n, L) with n and L in (x, y[, z]) order."""
+        dim = len(grids[0][0])
+        self.count = len(grids)
+        self.dim = dim
+        self.prec = prec
+        self.dtype = np.complex64 if prec == "f32" else np.complex128
+        self.grids = []
+        na, La = [], []
+        for n, L in grids:
+            n = tuple(int(v) for v in n)
+            L = (float(L),) * dim if np.isscalar(L) else tuple(float(v) for v in L)
+            self.grids.append((n, L))
+            na += list(n)
+            La += list(L)
+        out = ctypes.c_void_p()
+        st = lib().sgp_ensemble_create(dim, self.count, (ctypes.c_int * len(na))(*na),
+                                       (ctypes.c_double * len(La))(*La), PRECS[prec],
+                                       int(device), ctypes.c_void_p(stream or 0), ctypes.byref(out))
+        _echeck(st, None)
+        self.handle = out
+
+    @property
+    def groups(self):
+        return lib().sgp_ensemble_groups(self.handle)
+
+    def set_params(self, plist):
+        arr = (Params * self.count)(*[_params(d) for d in plist])
+        _echeck(lib().sgp_ensemble_set_params(self.handle, arr), self.handle)
+
+    def set_member_state(self, m, src, t0=0.0):
+        ptr, dev, _keep = _ptr(src, self.dtype)
+        _echeck(lib().sgp_ensemble_set_member_state(self.handle, int(m), ctypes.c_void_p(ptr), dev,
+                                                    float(t0)), self.handle)
+
+    def get_member_state(self, m, out=None):
+        n, _ = self.grids[m]
+        if out is None:
+            out = np.empty((5,) + n[::-1], dtype=self.dtype)
+        ptr, dev, _keep = _ptr(out, self.dtype)
+        _echeck(lib().sgp_ensemble_get_member_state(self.handle, int(m), ctypes.c_void_p(ptr), dev),
+                self.handle)
+        return out
+
+    def step(self, nsteps, dt, scheme="ts2"):
+        s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        _echeck(lib().sgp_ensemble_step(self.handle, int(nsteps), float(dt), s), self.handle)
+
+    def observables(self):
+        arr = (Obs * self.count)()
+        _echeck(lib().sgp_ensemble_observables(self.handle, arr), self.handle)
+        return [o.as_dict() for o in arr]
+
+    def synchronize(self):
+        _echeck(lib().sgp_ensemble_synchronize(self.handle), self.handle)
+
+    def launch_count(self):
+        return int(lib().sgp_ensemble_launch_count(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().sgp_ensemble_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

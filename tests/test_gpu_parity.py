@@ -243,3 +243,66 @@ def test_zero_field_stays_zero():
     assert np.array_equal(c.get_state(), z)
     ob = c.observables()[0]
     assert ob["mass"] == 0.0 and ob["energy"] == 0.0
+
+
+# ----------------------------------------------------------------------------
+# per-member parameters, graph replay, ensembles of different grids
+# ----------------------------------------------------------------------------
+def test_per_member_parameters_f64():
+    n, L = (48, 32), (6.0, 5.0)
+    plist = [_params(omega=0.2, gamma=0.5, c0=40.0, gx=1.1),
+             _params(omega=0.7, gamma=1.4, c0=90.0, c1=2.0, gy=0.8),
+             _params(omega=0.2, gamma=0.5, c0=10.0, c2=-3.0)]
+    psis = [inputs.gaussian_random_phase(n, L, seed=30 + k, amp=0.4) for k in range(3)]
+    c = sgp.Context(n, L, batch=3, prec="f64")
+    c.set_params_batch(plist)
+    c.set_state(np.stack(psis), 0.0)
+    c.step(12, 2e-3, "ts4")
+    out = c.get_state()
+    obs = c.observables()
+    for k in range(3):
+        ref, t = _oracle_run(n, L, plist[k], psis[k], 12, 2e-3, "ts4")
+        assert O.rel_l2(out[k], ref) < 1e-10
+        r = O.observables(ref, O.Grid(n, L), O.Params(**plist[k]), t)
+        assert abs(obs[k]["energy"] - r["energy"]) < 1e-10 * max(1, abs(r["energy"]))
+
+
+@pytest.mark.parametrize("scheme", ["ts2", "ts4"])
+def test_graph_replay_matches_direct_issue_and_oracle(scheme):
+    n, L = (32, 32), 6.0
+    prm = _params(gx=1.2, gy=0.9)
+    psi = inputs.gaussian_random_phase(n, L, seed=15, amp=0.3)
+    outs = []
+    for graphs in (True, False):
+        c = sgp.Context(n, L, prec="f64")
+        c.set_params(**prm)
+        c.set_graphs(graphs)
+        c.set_state(psi[None].copy(), 0.0)
+        c.step(150, 1e-3, scheme)          # 2 graph chunks of 64 + 22 direct
+        outs.append(c.get_state()[0])
+        assert abs(c.t - 0.15) < 1e-14
+        c.close()
+    assert O.rel_l2(outs[0], outs[1]) < 1e-13
+    ref, _ = _oracle_run(n, L, prm, psi, 150, 1e-3, scheme)
+    assert O.rel_l2(outs[0], ref) < 1e-10
+
+
+def test_ensemble_of_different_grids_f64():
+    grids = [((32, 32), 6.0), ((48, 48), 7.0), ((32, 32), 6.0), ((64, 32), (8.0, 5.0))]
+    rng = np.random.default_rng(5)
+    plist = [_params(omega=float(rng.uniform(0, 0.9)), gamma=float(rng.uniform(0, 2)),
+                     c0=float(rng.uniform(50, 200)), c1=float(rng.uniform(-5, 5)),
+                     c2=float(rng.uniform(0, 10))) for _ in grids]
+    psis = [inputs.gaussian_random_phase(n, L, seed=50 + k, amp=0.3) for k, (n, L) in enumerate(grids)]
+    with sgp.Ensemble(grids, prec="f64") as ens:
+        assert ens.groups == 3
+        ens.set_params(plist)
+        for k, psi in enumerate(psis):
+            ens.set_member_state(k, psi.copy(), 0.0)
+        ens.step(70, 1e-3, "ts2")           # one graph chunk of 64 + 6 direct
+        obs = ens.observables()
+        for k, ((n, L), psi) in enumerate(zip(grids, psis)):
+            ref, t = _oracle_run(n, L, plist[k], psi, 70, 1e-3, "ts2")
+            assert O.rel_l2(ens.get_member_state(k), ref) < 1e-10
+            r = O.observables(ref, O.Grid(n, L), O.Params(**plist[k]), t)
+            assert abs(obs[k]["mass"] - r["mass"]) < 1e-12
