@@ -72,6 +72,31 @@ def bytes_per_point_step(dim, scheme, prec):
     return 2 * s * passes * pairs, 2 * s
 
 
+def csrc_hash():
+    """Hash of the CUDA sources (identifies the kernels the counters came from)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2603_25282_gb300", "csrc", "*"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(wl, kernel):
+    """DRAM bytes per launch from the committed ncu capture, or None when the
+    kernels have changed since it was taken (or none exists)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+    except Exception:
+        return None
+    if tr.get("csrc_sha256_16") != csrc_hash():
+        return None
+    return tr.get("bytes_per_launch", {}).get("%s:%s" % (wl, kernel))
+
+
 # ---------------------------------------------------------------------------
 # clocks sampling (nvidia-smi, during the timed region)
 # ---------------------------------------------------------------------------
@@ -277,16 +302,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kinds, key=lambda k: kinds[k][1])
     dom_avg_ms = kinds[dom][1] / kinds[dom][0]
     achieved = per_pass_bytes / (dom_avg_ms * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(tr_path) as f:
-            tr = json.load(f)
-        key = "%s:%s" % (wl, dom)
-        if key in tr:
-            traffic = tr[key]
-    except Exception:
-        pass
+    traffic = measured_traffic(wl, dom)
     bpp, bmin = bytes_per_point_step(dim, scheme, prec)
     step_gbs = bpp * pts * batch * args.steps / (ms * 1e-3) / 1e9
 
