@@ -135,6 +135,16 @@ template <typename R> __device__ __forceinline__ int padx(int idx) {
 template <typename R> __host__ __device__ constexpr int line_pad(int N) {
   return N + (N >> PadShift<R>::value) + 1;
 }
+// Padded line length for TILE lines exchanged side by side (the line pass):
+// a warp holds 32/TILE positions of TILE lines, so the line-to-line offset
+// decides the banks.  Counting the shared-memory wavefronts of every exchange
+// of the Stockham stages gives the fewest with +1 except: FP32 TILE = 8, +2
+// (1024 instead of 1792 per N = 512 CTA); FP32 TILE = 4, +4 (1536 instead of
+// 3072 at N = 1024); FP64 TILE = 4, +2 (2048 instead of 2176 at N = 512).
+template <typename R> __host__ __device__ constexpr int line_pad_tile(int N, int TILE) {
+  return N + (N >> PadShift<R>::value) +
+         (sizeof(R) == 4 ? (TILE == 8 ? 2 : (TILE == 4 ? 4 : 1)) : (TILE == 4 ? 2 : 1));
+}
 
 // ----------------------------------------------------------------------------
 // small DFTs, DIR = -1 forward, +1 inverse

@@ -413,7 +413,7 @@ struct LCfg {
   static constexpr int TMIN = sizeof(R) == 4 ? 4 : 2;
   static constexpr int TILE = (512 / T) > TMAX ? TMAX : ((512 / T) < TMIN ? TMIN : (512 / T));
   static constexpr int THREADS = TILE * T;
-  static constexpr int LP = line_pad<R>(N);
+  static constexpr int LP = line_pad_tile<R>(N, TILE);
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * TILE * LP);
   static constexpr int MINB = (THREADS <= 256 && 2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
