@@ -65,6 +65,18 @@ template <typename C> __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x
   return fma(a.x, a.x, a.y * a.y);
 }
 
+// FP32: the lane-wise operations as packed two-lane instructions (one issue
+// slot for both parts).  Each lane rounds exactly like the scalar form:
+// a - b is the fused b*(-1) + a, exact before its single rounding.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ float2 caxpy(float2 acc, float2 a, float s) {
+  return __ffma2_rn(a, make_float2(s, s), acc);
+}
+
 // ----------------------------------------------------------------------------
 // radix plans
 // ----------------------------------------------------------------------------
