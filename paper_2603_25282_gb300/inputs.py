@@ -111,3 +111,24 @@ def ensemble_members(count, seed, sides=(64, 96, 128, 192, 256)):
                         c2=float(rng.uniform(0.0, 10.0)),
                         gx=1.0, gy=1.0, gz=1.0, seed=int(seed) * 100003 + i))
     return out
+
+
+def density_target(n, L, seed):
+    """Seeded target of the terminal density misfit (the adjoint workload).
+
+    Component l gets rho_l(x) = w_l exp(-|x - c_l|^2), i.e. G(x - c_l)^2 with
+    G = exp(-|x|^2/2), centre c_l ~ U[-1/2, 1/2]^d (PCG64 seeded with
+    ``seed``) and w_l such that h^d sum_j rho_l(x_j) = 1/5 on the grid, so the
+    five targets carry mass 1 together.  Returns (centres (5, d), weights (5,)).
+    The objective evaluates rho_l at the rotated point R(T) x itself.
+    """
+    X, h = coords(n, L)
+    rng = np.random.default_rng(seed)
+    d = len(X)
+    centres = rng.uniform(-0.5, 0.5, size=(5, d))
+    cell = float(np.prod(h))
+    weights = np.empty(5)
+    for comp in range(5):
+        r2 = sum((x - c) ** 2 for x, c in zip(X, centres[comp]))
+        weights[comp] = 0.2 / (cell * float(np.sum(np.exp(-r2))))
+    return centres, weights
