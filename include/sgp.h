@@ -171,6 +171,37 @@ sgp_status sgp_substep(sgp_ctx* ctx, int kind, double delta);
 sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
 
 /* ---------------------------------------------------------------------
+ * Adjoint (gradients of a terminal-time objective J(Phi(T))).
+ * ------------------------------------------------------------------- */
+/* Like sgp_step, and also stores the state at the start of every chunk of
+ * `interval` steps (interval = 0: ceil(sqrt(nsteps))) in device memory
+ * owned by the context, for sgp_backward.  The record stays valid until the
+ * next sgp_set_state, sgp_set_params(_batch), sgp_step, sgp_substep or
+ * sgp_record.  Memory: ceil(nsteps/interval) states for the checkpoints and
+ * interval*(substeps per step) + 1 states (3 for TS2, 7 for TS4) for one
+ * recomputed segment in sgp_backward.  Errors: SGP_EINVAL for nsteps <= 0,
+ * interval < 0 or dt/scheme as in sgp_step; SGP_ESTATE before
+ * sgp_set_state; SGP_ENOMEM/SGP_ECUDA on allocation or launch failure. */
+sgp_status sgp_record(sgp_ctx* ctx, long long nsteps, double dt, int scheme,
+                      long long interval);
+
+/* Vector-Jacobian product of the recorded run (Sec. 3.3 compositions taken
+ * substep by substep in reverse; the flows of Eqs. (sl1) and (solution2)
+ * are exact, time-reversible and symplectic).  g_T: dJ/dRe Phi(T) +
+ * i dJ/dIm Phi(T) in the state layout (batch, 5, [nz,] ny, nx) and precision
+ * of the context, on the device if g_T_on_device, else on the host.  Writes
+ * the same quantity for the state at the start of the record into g_0
+ * (device if g_0_on_device; may alias g_T) and, if dparams is not NULL, the
+ * partial derivatives dJ/d(Omega, gamma, c0, c1, c2) through the dynamics
+ * into dparams[5*m + 0..4] for member m (host memory; a dependence of J on
+ * Omega through the frame R(T) is the caller's).  Each segment is recomputed
+ * from its checkpoint.  Synchronises the context stream.  The record stays
+ * valid (several objectives can be differentiated).  Errors: SGP_EINVAL for
+ * NULL buffers; SGP_ESTATE without a valid record; SGP_ECUDA. */
+sgp_status sgp_backward(sgp_ctx* ctx, const void* g_T, int g_T_on_device, void* g_0,
+                        int g_0_on_device, double* dparams);
+
+/* ---------------------------------------------------------------------
  * Ensembles: independent runs on different grids advanced together.
  * Members are grouped by grid; each group is one batched context.  A step
  * of the ensemble issues every group's passes; runs of 64 steps or more

@@ -28,6 +28,7 @@ UNITS = [
     ("inst_f32_l", "sgp_inst.cu", ["-DSGP_REAL=float", "-DSGP_PART=1"]),
     ("inst_f64_x", "sgp_inst.cu", ["-DSGP_REAL=double", "-DSGP_PART=0"]),
     ("inst_f64_l", "sgp_inst.cu", ["-DSGP_REAL=double", "-DSGP_PART=1"]),
+    ("adjoint", "sgp_adjoint.cu", []),
     ("api", "sgp_api.cu", []),
 ]
 

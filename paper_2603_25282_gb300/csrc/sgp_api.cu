@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/sgp.h"
+#include "sgp_adjoint.cuh"
 #include "sgp_launch.cuh"
 
 using namespace sgp;
@@ -203,6 +204,27 @@ MemberPrm member_prm(const sgp_params& p, int dim) {
   return m;
 }
 
+// Recorded trajectory for the adjoint: the state every `interval` steps
+// (sqrt(nsteps) by default) and the device buffers of the backward sweep.
+struct AdjRec {
+  bool valid = false;
+  long long nsteps = 0, interval = 0, nck = 0;
+  double dt = 0.0, t0 = 0.0;
+  int scheme = 0;
+  void* ckpt = nullptr;            // nck states
+  size_t ckpt_cap = 0;
+  void* seg = nullptr;             // the states of one recomputed segment
+  size_t seg_cap = 0;
+  void* g = nullptr;               // adjoint state
+  size_t g_cap = 0;
+  void* spec = nullptr;            // transform of a substep output
+  size_t spec_cap = 0;
+  double* dp = nullptr;            // [batch][GP_N]
+  size_t dp_cap = 0;
+  double* part = nullptr;          // per-block partial sums
+  size_t part_cap = 0;
+};
+
 }  // namespace
 
 struct sgp_ctx {
@@ -236,6 +258,7 @@ struct sgp_ctx {
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
   std::vector<cudaEvent_t> event_pool;
+  AdjRec adj;
   std::string err;
 };
 
@@ -389,9 +412,9 @@ sgp_status get_tables(sgp_ctx* c, double delta, const LinTables** out) {
 // passes
 // ----------------------------------------------------------------------------
 template <typename R>
-sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
+sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
   XPassArgs<R> a{};
-  a.field = (cplx<R>*)c->field;
+  a.field = (cplx<R>*)field;
   a.tw = (const TwE<R>*)c->tw[0];
   a.ntot = c->ntot;
   a.rows = c->n[1] * c->n[2];
@@ -413,11 +436,16 @@ sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
   return SGP_OK;
 }
 
+template <typename R>
+sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
+  return x_pass_on<R>(c, c->field, mode, delta, t_off);
+}
+
 // axis 1: lines along y (planes = z slices); axis 2: lines along z (planes = y rows)
 template <typename R>
-sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
+sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTables* t) {
   LPassArgs<R> a{};
-  a.field = (cplx<R>*)c->field;
+  a.field = (cplx<R>*)field;
   a.tw = (const TwE<R>*)c->tw[axis];
   a.ntot = c->ntot;
   a.nx = c->n[0];
@@ -452,20 +480,30 @@ sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
   return SGP_OK;
 }
 
+template <typename R>
+sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
+  return line_pass_on<R>(c, c->field, axis, mode, t);
+}
+
 // Linear flow over delta between x-passes.  Entry: x-spectral (the x-pass
 // has done its forward transform).  Exit: x-spectral.
 template <typename R>
-sgp_status linear_middle(sgp_ctx* c, double delta) {
+sgp_status linear_middle_on(sgp_ctx* c, void* f, double delta) {
   const LinTables* t = nullptr;
   SGP_TRY(get_tables<R>(c, delta, &t));
   if (c->dim == 2) {
-    SGP_TRY(line_pass<R>(c, 1, LP_FWD | LP_MIX | LP_INV, t));
+    SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD | LP_MIX | LP_INV, t));
   } else {
-    SGP_TRY(line_pass<R>(c, 1, LP_FWD, nullptr));
-    SGP_TRY(line_pass<R>(c, 2, LP_FWD | LP_MIX | LP_INV, t));
-    SGP_TRY(line_pass<R>(c, 1, LP_INV, nullptr));
+    SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD, nullptr));
+    SGP_TRY(line_pass_on<R>(c, f, 2, LP_FWD | LP_MIX | LP_INV, t));
+    SGP_TRY(line_pass_on<R>(c, f, 1, LP_INV, nullptr));
   }
   return SGP_OK;
+}
+
+template <typename R>
+sgp_status linear_middle(sgp_ctx* c, double delta) {
+  return linear_middle_on<R>(c, c->field, delta);
 }
 
 // substep pattern of one step, Sec. 3.3
@@ -592,6 +630,213 @@ sgp_status substep(sgp_ctx* c, int kind, double delta) {
     SGP_TRY(linear_middle<R>(c, delta));
     SGP_TRY(x_pass<R>(c, XP_INV, 0.0, 0.0));
     c->t += delta;
+  }
+  return SGP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// adjoint: checkpointed record and backward sweep
+// ----------------------------------------------------------------------------
+size_t state_bytes(const sgp_ctx* c) { return (size_t)c->batch * 5 * c->ntot * c->elem; }
+
+sgp_status ensure_buf(sgp_ctx* c, void** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes && *p) return SGP_OK;
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  SGP_CUDA(c, cudaMalloc(p, bytes));
+  *cap = bytes;
+  return SGP_OK;
+}
+
+void free_adj(sgp_ctx* c) {
+  AdjRec& r = c->adj;
+  cudaFree(r.ckpt);
+  cudaFree(r.seg);
+  cudaFree(r.g);
+  cudaFree(r.spec);
+  cudaFree(r.dp);
+  cudaFree(r.part);
+  r = AdjRec();
+}
+
+// Forward run of nsteps that stores the state at the start of every chunk
+// of `interval` steps.  The chunks run on the ordinary step path.
+template <typename R>
+sgp_status record_steps(sgp_ctx* c, long long nsteps, double dt, int scheme, long long interval) {
+  AdjRec& r = c->adj;
+  r.valid = false;
+  if (interval <= 0) interval = (long long)std::ceil(std::sqrt((double)nsteps));
+  if (interval > nsteps) interval = nsteps;
+  const long long nck = (nsteps + interval - 1) / interval;
+  const size_t sb = state_bytes(c);
+  SGP_TRY(ensure_buf(c, &r.ckpt, &r.ckpt_cap, sb * (size_t)nck));
+  r.t0 = c->t;
+  for (long long k = 0; k < nck; ++k) {
+    SGP_CUDA(c, cudaMemcpyAsync((char*)r.ckpt + sb * (size_t)k, c->field, sb,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    const long long n = std::min(interval, nsteps - k * interval);
+    SGP_TRY(run_steps<R>(c, n, dt, scheme));
+  }
+  r.nsteps = nsteps;
+  r.interval = interval;
+  r.nck = nck;
+  r.dt = dt;
+  r.scheme = scheme;
+  r.valid = true;
+  return SGP_OK;
+}
+
+// physical space -> unnormalised full transform (all axes)
+template <typename R>
+sgp_status to_spectral(sgp_ctx* c, void* f) {
+  SGP_TRY(x_pass_on<R>(c, f, XP_FWD, 0.0, 0.0));
+  SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD, nullptr));
+  if (c->dim == 3) SGP_TRY(line_pass_on<R>(c, f, 2, LP_FWD, nullptr));
+  return SGP_OK;
+}
+
+sgp_status accum(sgp_ctx* c, int nblocks, int nterm, const int* slots) {
+  c->launches++;
+  SGP_CUDA(c, launch_accum_params(c->adj.part, nblocks, nterm, c->batch, slots, c->adj.dp,
+                                  c->stream));
+  return SGP_OK;
+}
+
+// g <- (D N_d(Phi_in))^T g at Phi_out = phi, and the parameter terms
+template <typename R>
+sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t) {
+  NLAdjArgs<R> a{};
+  a.g = (cplx<R>*)c->adj.g;
+  a.phi = (const cplx<R>*)phi;
+  a.ntot = c->ntot;
+  a.nx = c->n[0];
+  a.ny = c->n[1];
+  a.x0 = -c->L[0];
+  a.hx = c->h[0];
+  a.y0 = -c->L[1];
+  a.hy = c->h[1];
+  a.z0 = c->dim == 3 ? -c->L[2] : 0.0;
+  a.hz = c->dim == 3 ? c->h[2] : 0.0;
+  a.delta = delta;
+  a.t = t;
+  a.mp = c->mp_dev;
+  a.partials = c->adj.part;
+  a.nblocks = adjoint_blocks(c->ntot);
+  c->launches++;
+  {
+    ProfScope ps(c, PK_OTHER);
+    SGP_CUDA(c, launch_nl_adjoint<R>(a, c->batch, c->stream));
+  }
+  const int slots[4] = {GP_OMEGA, GP_C0, GP_C1, GP_C2};
+  return accum(c, a.nblocks, NLA_NT, slots);
+}
+
+// g <- L(-d) g, and the Omega and gamma terms from the transforms of g and
+// of Phi_out
+template <typename R>
+sgp_status adjoint_linear(sgp_ctx* c, const void* phi, double delta) {
+  AdjRec& r = c->adj;
+  SGP_CUDA(c, cudaMemcpyAsync(r.spec, phi, state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  SGP_TRY(to_spectral<R>(c, r.spec));
+  SGP_TRY(to_spectral<R>(c, r.g));
+  LinParArgs<R> a{};
+  a.g = (const cplx<R>*)r.g;
+  a.s = (const cplx<R>*)r.spec;
+  a.ntot = c->ntot;
+  a.NX = c->n[0];
+  a.NY = c->n[1];
+  a.Lx = c->L[0];
+  a.Ly = c->L[1];
+  a.delta = delta;
+  a.scale = 1.0 / (double)c->ntot;
+  a.mp = c->mp_dev;
+  a.partials = r.part;
+  a.nblocks = adjoint_blocks(c->ntot);
+  c->launches++;
+  {
+    ProfScope ps(c, PK_OTHER);
+    SGP_CUDA(c, launch_lin_param<R>(a, c->batch, c->stream));
+  }
+  const int slots[2] = {GP_OMEGA, GP_GAMMA};
+  SGP_TRY(accum(c, a.nblocks, LPA_NT, slots));
+  // the linear flow over -delta on the transformed g, then back to space
+  const LinTables* t = nullptr;
+  SGP_TRY(get_tables<R>(c, -delta, &t));
+  if (c->dim == 2) {
+    SGP_TRY(line_pass_on<R>(c, r.g, 1, LP_MIX | LP_INV, t));
+  } else {
+    SGP_TRY(line_pass_on<R>(c, r.g, 2, LP_MIX | LP_INV, t));
+    SGP_TRY(line_pass_on<R>(c, r.g, 1, LP_INV, nullptr));
+  }
+  return x_pass_on<R>(c, r.g, XP_INV, 0.0, 0.0);
+}
+
+struct SubRec {
+  char kind;
+  double delta;
+  double toff;     // time of the substep relative to the segment start
+};
+
+// Backward sweep over the recorded trajectory: each segment is recomputed
+// from its checkpoint substep by substep (unmerged), then g is carried back
+// through the segment's substeps in reverse order.
+template <typename R>
+sgp_status backward_sweep(sgp_ctx* c) {
+  AdjRec& r = c->adj;
+  const size_t sb = state_bytes(c);
+  const auto seq = scheme_seq(r.scheme);
+  const size_t per_seg = (size_t)r.interval * seq.size() + 1;
+  SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, sb * per_seg));
+  SGP_TRY(ensure_buf(c, &r.spec, &r.spec_cap, sb));
+  const size_t need_part = (size_t)c->batch * adjoint_blocks(c->ntot) * NLA_NT * sizeof(double);
+  SGP_TRY(ensure_buf(c, (void**)&r.part, &r.part_cap, need_part));
+  for (const auto& st : seq)
+    if (st.first == 'L') {
+      const LinTables* t = nullptr;
+      SGP_TRY(get_tables<R>(c, st.second * r.dt, &t));
+      SGP_TRY(get_tables<R>(c, -st.second * r.dt, &t));
+    }
+  std::vector<SubRec> subs;
+  for (long long k = r.nck - 1; k >= 0; --k) {
+    const long long n = std::min(r.interval, r.nsteps - k * r.interval);
+    const double tk = r.t0 + (double)(k * r.interval) * r.dt;
+    c->launches++;
+    k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, tk);
+    SGP_CUDA(c, cudaGetLastError());
+    char* seg = (char*)r.seg;
+    SGP_CUDA(c, cudaMemcpyAsync(seg, (const char*)r.ckpt + sb * (size_t)k, sb,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    subs.clear();
+    double toff = 0.0;
+    for (long long s = 0; s < n; ++s) {
+      const double tstep = (double)s * r.dt;
+      double sub = 0.0;
+      for (const auto& st : seq) {
+        const size_t j = subs.size();
+        void* out = seg + sb * (j + 1);
+        SGP_CUDA(c, cudaMemcpyAsync(out, seg + sb * j, sb, cudaMemcpyDeviceToDevice, c->stream));
+        const double delta = st.second * r.dt;
+        toff = tstep + sub * r.dt;
+        if (st.first == 'N') {
+          SGP_TRY(x_pass_on<R>(c, out, XP_NL, delta, toff));
+        } else {
+          SGP_TRY(x_pass_on<R>(c, out, XP_FWD, 0.0, 0.0));
+          SGP_TRY(linear_middle_on<R>(c, out, delta));
+          SGP_TRY(x_pass_on<R>(c, out, XP_INV, 0.0, 0.0));
+          sub += st.second;
+        }
+        subs.push_back({st.first, delta, toff});
+      }
+    }
+    for (size_t j = subs.size(); j-- > 0;) {
+      const void* phi_out = seg + sb * (j + 1);
+      if (subs[j].kind == 'N')
+        SGP_TRY(adjoint_nonlinear<R>(c, phi_out, subs[j].delta, tk + subs[j].toff));
+      else
+        SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta));
+    }
   }
   return SGP_OK;
 }
@@ -851,6 +1096,7 @@ sgp_status sgp_set_params(sgp_ctx* c, const sgp_params* p) {
   if (!p) return fail(c, SGP_EINVAL, "NULL params");
   if (!finite_params(p)) return fail(c, SGP_EINVAL, "non-finite parameter");
   DeviceGuard guard(c->device);
+  c->adj.valid = false;
   c->prm.assign(c->batch, *p);
   return upload_params(c);
 }
@@ -862,6 +1108,7 @@ sgp_status sgp_set_params_batch(sgp_ctx* c, const sgp_params* p, int count) {
   for (int m = 0; m < count; ++m)
     if (!finite_params(&p[m])) return fail(c, SGP_EINVAL, "non-finite parameter (member %d)", m);
   DeviceGuard guard(c->device);
+  c->adj.valid = false;
   c->prm.assign(p, p + count);
   return upload_params(c);
 }
@@ -876,6 +1123,7 @@ sgp_status sgp_set_state(sgp_ctx* c, const void* src, int src_on_device, double 
                               src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               c->stream));
   if (!src_on_device) SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->adj.valid = false;
   c->t = t0;
   c->have_state = true;
   return SGP_OK;
@@ -907,8 +1155,44 @@ sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_step before sgp_set_state");
   if (nsteps == 0) return SGP_OK;
   DeviceGuard guard(c->device);
+  c->adj.valid = false;
   return c->prec == SGP_F32 ? run_steps<float>(c, nsteps, dt, scheme)
                             : run_steps<double>(c, nsteps, dt, scheme);
+}
+
+sgp_status sgp_record(sgp_ctx* c, long long nsteps, double dt, int scheme, long long interval) {
+  if (!c) return SGP_EINVAL;
+  if (nsteps <= 0) return fail(c, SGP_EINVAL, "nsteps must be positive");
+  if (interval < 0) return fail(c, SGP_EINVAL, "interval < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SGP_EINVAL, "dt must be positive and finite");
+  if (scheme != SGP_TS2 && scheme != SGP_TS4) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
+  if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_record before sgp_set_state");
+  DeviceGuard guard(c->device);
+  return c->prec == SGP_F32 ? record_steps<float>(c, nsteps, dt, scheme, interval)
+                            : record_steps<double>(c, nsteps, dt, scheme, interval);
+}
+
+sgp_status sgp_backward(sgp_ctx* c, const void* g_T, int g_T_on_device, void* g_0,
+                        int g_0_on_device, double* dparams) {
+  if (!c) return SGP_EINVAL;
+  if (!g_T || !g_0) return fail(c, SGP_EINVAL, "NULL gradient buffer");
+  if (!c->adj.valid) return fail(c, SGP_ESTATE, "sgp_backward without a valid sgp_record");
+  DeviceGuard guard(c->device);
+  AdjRec& r = c->adj;
+  const size_t sb = state_bytes(c);
+  SGP_TRY(ensure_buf(c, &r.g, &r.g_cap, sb));
+  SGP_TRY(ensure_buf(c, (void**)&r.dp, &r.dp_cap, sizeof(double) * GP_N * c->batch));
+  SGP_CUDA(c, cudaMemcpyAsync(r.g, g_T, sb, g_T_on_device ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyHostToDevice, c->stream));
+  SGP_CUDA(c, cudaMemsetAsync(r.dp, 0, sizeof(double) * GP_N * c->batch, c->stream));
+  SGP_TRY(c->prec == SGP_F32 ? backward_sweep<float>(c) : backward_sweep<double>(c));
+  SGP_CUDA(c, cudaMemcpyAsync(g_0, r.g, sb, g_0_on_device ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost, c->stream));
+  if (dparams)
+    SGP_CUDA(c, cudaMemcpyAsync(dparams, r.dp, sizeof(double) * GP_N * c->batch,
+                                cudaMemcpyDeviceToHost, c->stream));
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SGP_OK;
 }
 
 sgp_status sgp_set_graphs(sgp_ctx* c, int enable) {
@@ -924,6 +1208,7 @@ sgp_status sgp_substep(sgp_ctx* c, int kind, double delta) {
   if (!std::isfinite(delta)) return fail(c, SGP_EINVAL, "non-finite delta");
   if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_substep before sgp_set_state");
   DeviceGuard guard(c->device);
+  c->adj.valid = false;
   return c->prec == SGP_F32 ? substep<float>(c, kind, delta) : substep<double>(c, kind, delta);
 }
 
@@ -985,6 +1270,7 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   if (c->stream || c->own_stream) cudaStreamSynchronize(c->stream);
   free_graphs(c);
   free_tables(c);
+  free_adj(c);
   cudaFree(c->field);
   for (void* t : c->tw) cudaFree(t);
   cudaFree(c->t_dev);

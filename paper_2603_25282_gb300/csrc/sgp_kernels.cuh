@@ -216,6 +216,47 @@ __device__ __forceinline__ C unit_dir(C u, R& mag) {
   return mkc((R)1, (R)0);
 }
 
+// SU(2) parameters of the spin rotation exp(-i c1 d F.f) of Eq. (solution2):
+// U = cos(k/2) - i sin(k/2) Fhat.sigma, k = c1 d |F|, so U11 = cos(k/2) - i q Fz
+// and U12 = -i q conj(F+), q = sin(k/2)/|F|.  ahat - 1 and cp - 1 are formed
+// without cancellation:
+//   cp - 1 = -q^2 |F+|^2 / (1 + cp),  ahat - 1 = (cos - cp - i q Fz)/cp,
+//   cos - cp = -q^2 Fz^2 / (cos + cp).
+// Also returns sin and cos of k/2 and 1/|F|.  False (U = I) when F = 0.
+template <typename R>
+struct SpinRot {
+  cplx<R> am1, bhat;
+  R cpm1, sp;
+  R sh, ch, rFn, Fn;
+};
+
+template <typename R>
+__device__ __forceinline__ bool spin_rotation(R Fz, cplx<R> Fp, R c1, R delta, SpinRot<R>& o) {
+  const R Fp2 = cabs2(Fp);
+  const R F2 = Fp2 + Fz * Fz;
+  if (!(F2 > (R)0)) return false;
+  const R rFn = rsqrt_r(F2);
+  const R Fn = F2 * rFn;
+  R sh, ch;
+  sincos_small((R)0.5 * c1 * delta * Fn, &sh, &ch);
+  const R q = sh * rFn;
+  const R qFz = q * Fz;
+  const R cp2 = ch * ch + qFz * qFz;
+  const R icp = rsqrt_r(cp2);
+  const R cp = cp2 * icp;
+  o.cpm1 = -(q * q * Fp2) * rcp_r((R)1 + cp);
+  const R cmc = ch > (R)0 ? -(qFz * qFz) * rcp_r(ch + cp) : ch - cp;   // cos - cp
+  o.am1 = mkc(cmc * icp, -qFz * icp);
+  R mag;
+  o.bhat = unit_dir(mkc(-Fp.y, -Fp.x), mag);   // direction of -i conj(F+)
+  o.sp = q * mag;
+  o.sh = sh;
+  o.ch = ch;
+  o.rFn = rFn;
+  o.Fn = Fn;
+  return true;
+}
+
 // ----------------------------------------------------------------------------
 // exact nonlinear flow at one point (Sec. 3.2, Eq. (solution2))
 // ----------------------------------------------------------------------------
@@ -262,30 +303,12 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
       b[k] = cadd(v[k], inc[k]);
     }
   }
-  // (2) spin rotation exp(-i c1 d F.f): spin-2 image of
-  //     U = cos(k/2) - i sin(k/2) Fhat.sigma, k = c1 d |F|:
-  //     U11 = cos(k/2) - i q Fz, U12 = -i q conj(F+), q = sin(k/2)/|F|.
-  //     ahat - 1 and cp - 1 are formed without cancellation:
-  //       cp - 1 = -q^2 |F+|^2 / (1 + cp),  ahat - 1 = (cos - cp - i q Fz)/cp,
-  //       cos - cp = -q^2 Fz^2 / (cos + cp)
-  const R Fp2 = cabs2(Fp);
-  const R F2 = Fp2 + Fz * Fz;
-  if (F2 > (R)0) {
-    const R rFn = rsqrt_r(F2);
-    const R Fn = F2 * rFn;
-    R sh, ch;
-    sincos_small((R)0.5 * c1 * delta * Fn, &sh, &ch);
-    const R q = sh * rFn;
-    const R qFz = q * Fz;
-    const R cp2 = ch * ch + qFz * qFz;
-    const R icp = rsqrt_r(cp2);
-    const R cp = cp2 * icp;
-    const R cpm1 = -(q * q * Fp2) * rcp_r((R)1 + cp);
-    const R cmc = ch > (R)0 ? -(qFz * qFz) * rcp_r(ch + cp) : ch - cp;   // cos - cp
-    const C am1 = mkc(cmc * icp, -qFz * icp);
-    R mag;
-    const C bhat = unit_dir(mkc(-Fp.y, -Fp.x), mag);   // direction of -i conj(F+)
-    const R sp = q * mag;
+  // (2) spin rotation exp(-i c1 d F.f), applied as the increment of the
+  //     spin-2 image of its SU(2) element (spin_rotation)
+  SpinRot<R> sr;
+  if (spin_rotation<R>(Fz, Fp, c1, delta, sr)) {
+    const C am1 = sr.am1, bhat = sr.bhat;
+    const R cpm1 = sr.cpm1, sp = sr.sp;
     C e[5];
     spin2_increment<R>(b, am1, bhat, cpm1, sp, e);
 #pragma unroll

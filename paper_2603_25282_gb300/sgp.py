@@ -98,6 +98,8 @@ def lib():
         "sgp_destroy": (I, [P]),
         "sgp_observables_static": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                        I, I, ctypes.POINTER(Params), D, P, I, P, ctypes.POINTER(Obs)]),
+        "sgp_record": (I, [P, LL, D, I, LL]),
+        "sgp_backward": (I, [P, P, I, P, I, ctypes.POINTER(ctypes.c_double)]),
         "sgp_set_profiling": (I, [P, I]),
         "sgp_get_profile": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -196,6 +198,22 @@ def get_time(ctx):
 def step(ctx, nsteps, dt, scheme="ts2"):
     s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
     _check(lib().sgp_step(ctx, int(nsteps), float(dt), s), ctx)
+
+
+def record(ctx, nsteps, dt, scheme="ts2", interval=0):
+    """sgp_record: step with checkpoints every `interval` steps (0: sqrt)."""
+    s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+    _check(lib().sgp_record(ctx, int(nsteps), float(dt), s, int(interval)), ctx)
+
+
+def backward(ctx, g_T, g_0, dtype, batch=1):
+    """sgp_backward: g_0 <- VJP of the recorded run applied to g_T; returns
+    dJ/d(Omega, gamma, c0, c1, c2) per member as a (batch, 5) float64 array."""
+    pi, di, _k1 = _ptr(g_T, dtype)
+    po, do, _k2 = _ptr(g_0, dtype)
+    dp = (ctypes.c_double * (5 * batch))()
+    _check(lib().sgp_backward(ctx, ctypes.c_void_p(pi), di, ctypes.c_void_p(po), do, dp), ctx)
+    return np.array(dp[:], dtype=np.float64).reshape(batch, 5)
 
 
 def substep(ctx, kind, delta):
@@ -302,6 +320,17 @@ class Context:
 
     def substep(self, kind, delta):
         substep(self.handle, kind, delta)
+
+    def record(self, nsteps, dt, scheme="ts2", interval=0):
+        record(self.handle, nsteps, dt, scheme, interval)
+
+    def backward(self, g_T, out=None):
+        """(g_0, dparams) for the recorded run; g_T and out as in set_state /
+        get_state (numpy or torch, host or CUDA)."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        dp = backward(self.handle, g_T, out, self.dtype, self.batch)
+        return out, dp
 
     def observables(self):
         return observables(self.handle, self.batch)

@@ -54,4 +54,6 @@ def test_create_grid_rejects_bad_arguments_before_cuda(lib):
 def test_null_context_calls_are_rejected(lib):
     assert lib.sgp_step(None, 1, 0.1, 0) == 1
     assert lib.sgp_observables(None, None) == 1
+    assert lib.sgp_record(None, 10, 0.1, 0, 0) == 1
+    assert lib.sgp_backward(None, None, 0, None, 0, None) == 1
     assert lib.sgp_destroy(None) == 0
