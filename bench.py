@@ -47,7 +47,20 @@ WORKLOADS = {
                       dict(omega=0.7, gamma=1.0, c0=500.0, c1=-2.0, c2=5.0, gx=1.0, gy=1.0, gz=2.0),
                       "ts4", 1e-3, "f32", 4),
 }
+# adjoint workload: one bench step = one gradient of the terminal density
+# misfit (recorded forward run of GRAD_STEPS steps + backward sweep)
+GRAD_WORKLOADS = {
+    "grad256_ts2_f32": ((256, 256), 8.0,
+                        dict(omega=0.6, gamma=1.0, c0=400.0, c1=-1.0, c2=2.0, gx=1.0, gy=1.0, gz=1.0),
+                        "ts2", 1e-3, "f32", 2000),
+}
+# ensemble workload: members on grids of different sides, one bench step =
+# one Strang step of every member
+ENS_WORKLOADS = {
+    "ens256_ts2_f32": dict(count=256, seed=4, scheme="ts2", dt=1e-3, prec="f32"),
+}
 METRIC = "5-comp grid-pt*steps/s"
+GRAD_METRIC = "grads/s"
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -215,6 +228,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     wl = args.workload
+    if wl not in WORKLOADS:
+        why = ("the FP64 oracle has no adjoint; its gradient is central differences "
+               "(two full runs per derivative)") if wl in GRAD_WORKLOADS else (
+               "the oracle runs one grid at a time; see the per-grid workloads")
+        print(json.dumps({"impl": "reference", "unavailable": why}))
+        return 0
     n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
     # W untimed steps, then up to K timed steps within a bounded wall time
     v, d = run_oracle_sample(wl, max(1, args.steps), args.warmup, budget=90.0)
@@ -323,6 +342,11 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = rep.weak_throughput(batch * pts * e2e_steps, e2e_s)
 
+    # ---- FP32 vs FP64 (rank 0, N = 1, FP32 workloads) ----------------------
+    acc = None
+    if rank == 0 and world == 1 and prec == "f32" and dim == 2 and not args.no_accuracy:
+        acc = accuracy_block(wl, local_rank, stream, value)
+
     # ---- CPU baseline (rank 0, N = 1) --------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -359,8 +383,302 @@ def run_ours(args, rank, world, local_rank):
                     "note": "per step: set_state from pinned host, one step, get_state to pinned host"},
             "cpu_baseline": cpu,
         }
+        if acc is not None:
+            line["accuracy"] = acc
         print(json.dumps(line))
     ctx.close()
+    rep.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# FP32 vs FP64 accuracy and speed (default workload)
+# ---------------------------------------------------------------------------
+def accuracy_block(wl, device, stream, f32_value, steps=1000, f64_batch=16, f64_steps=20):
+    """One member advanced `steps` steps in FP32 and in FP64 from the same
+    initial state: relative L2 of the field, mass drift of the FP32 run and
+    each observable's relative error against FP64; plus the FP64 throughput
+    of the same workload (batch f64_batch) for the FP32/FP64 speedup."""
+    import numpy as np
+    import torch
+
+    from paper_2603_25282_gb300 import inputs, sgp
+    n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
+    psi = inputs.gaussian_random_phase(n, L, seed=2, amp=0.01)[None]
+    res, obs = {}, {}
+    for pr in ("f32", "f64"):
+        c = sgp.Context(n, L, batch=1, prec=pr, device=device, stream=stream.cuda_stream)
+        c.set_params(**prm)
+        c.set_state(psi.astype(c.dtype).copy(), 0.0)
+        o0 = c.observables()[0]
+        c.step(steps, dt, scheme)
+        res[pr] = c.get_state()[0].astype(np.complex128)
+        obs[pr] = (o0, c.observables()[0])
+        c.close()
+    rel = float(np.linalg.norm(res["f32"] - res["f64"]) / np.linalg.norm(res["f64"]))
+    keys = ("mass", "energy", "magnetization", "lz", "e_kin", "e_pot", "e_rot", "e_int", "e_soc")
+    oerr = {}
+    for k in keys:
+        a, b = obs["f32"][1][k], obs["f64"][1][k]
+        oerr[k] = abs(a - b) / max(abs(b), 1e-300)
+    for i in range(3):
+        a, b = obs["f32"][1]["width2"][i], obs["f64"][1]["width2"][i]
+        if b:
+            oerr["width2_%d" % i] = abs(a - b) / abs(b)
+    m0 = obs["f32"][0]["mass"]
+    drift = abs(obs["f32"][1]["mass"] - m0) / m0
+    # FP64 throughput of the same workload
+    c = sgp.Context(n, L, batch=f64_batch, prec="f64", device=device, stream=stream.cuda_stream)
+    c.set_params(**prm)
+    host = np.stack([inputs.gaussian_random_phase(n, L, seed=m + 2, amp=0.01)
+                     for m in range(f64_batch)]).astype(np.complex128)
+    c.set_state(host, 0.0)
+    c.step(3, dt, scheme)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    c.step(f64_steps, dt, scheme)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    f64_value = f64_batch * math.prod(n) * f64_steps / (ev0.elapsed_time(ev1) * 1e-3)
+    c.close()
+    return {"steps": steps, "rel_l2_f32_vs_f64": rel, "mass_drift_f32": drift,
+            "obs_rel_err_f32_vs_f64": oerr, "f64_value": f64_value,
+            "f64_config": {"members": f64_batch, "steps": f64_steps},
+            "speedup_f32_over_f64": f32_value / f64_value}
+
+
+# ---------------------------------------------------------------------------
+# adjoint workload: gradients per second
+# ---------------------------------------------------------------------------
+def run_grad(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2603_25282_gb300 import inputs, sgp
+    from paper_2603_25282_gb300 import build as _build
+    from paper_2603_25282_gb300.autograd import density_misfit, propagate
+    from paper_2603_25282_gb300.replicas import Replicas
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    rep = Replicas("nccl", device=dev)
+    stream = torch.cuda.Stream(device=local_rank)
+    torch.cuda.set_stream(stream)
+    wl = args.workload
+    n, L, prm, scheme, dt, prec, nsteps = GRAD_WORKLOADS[wl]
+    T = nsteps * dt
+    ctx = sgp.Context(n, L, batch=1, prec=prec, device=local_rank, stream=stream.cuda_stream)
+    cdt = np.complex64 if prec == "f32" else np.complex128
+    host = inputs.gaussian_random_phase(n, L, seed=rep.member_seed(0, base=5), amp=0.01)[None].astype(cdt)
+    centres, weights = inputs.density_target(n, L, seed=6)
+    trap = (prm["gx"], prm["gy"], prm["gz"])
+    prm_vec = [prm[k] for k in ("omega", "gamma", "c0", "c1", "c2")]
+    psi_dev = torch.from_numpy(host).to(dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    def gradient(psi0):
+        p0 = psi0.detach().clone().requires_grad_(True)
+        pr = torch.tensor([prm_vec], dtype=torch.float64, device=dev, requires_grad=True)
+        phiT = propagate(ctx, p0, pr, nsteps, dt, scheme, trap=trap)
+        J = density_misfit(phiT[0], n, L, pr[0, 0], T, centres, weights)
+        J.backward()
+        return J, p0.grad, pr.grad
+
+    for _ in range(args.warmup):
+        gradient(psi_dev)
+    torch.cuda.synchronize()
+    rep.barrier()
+    l0 = ctx.launch_count()
+    total_ms = 0.0
+    with Clocks(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)                 # L2 flushed between timed gradients
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            J, g0, gp = gradient(psi_dev)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - l0
+    total_ms = rep.max_over_ranks(total_ms)
+    value = rep.weak_throughput(args.steps, total_ms * 1e-3)
+    clocks = clk.summary()
+
+    # forward alone (same steps, no record) for the adjoint overhead
+    ctx.set_params_batch([dict(zip(("omega", "gamma", "c0", "c1", "c2"), prm_vec),
+                               gx=trap[0], gy=trap[1], gz=trap[2])])
+    fwd_ms = 0.0
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        ctx.set_state(psi_dev, 0.0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ctx.step(nsteps, dt, scheme)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms += ev0.elapsed_time(ev1)
+    fwd_ms /= max(1, min(args.steps, 3))
+
+    # per-kernel split of one gradient
+    ctx.set_profiling(True)
+    gradient(psi_dev)
+    prof = ctx.get_profile()
+    ctx.set_profiling(False)
+    hbm_peak, peak_src = peaks()
+    state_bytes = host.nbytes
+    kinds = {k: v for k, v in prof.items() if k in ("xpass", "linepass_y") and v[0]}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    dom_avg = kinds[dom][1] / kinds[dom][0]
+    achieved = 2 * state_bytes / (dom_avg * 1e-3) / 1e9
+
+    # end to end: initial state from pinned host memory, gradients to host
+    pinned = torch.from_numpy(host).pin_memory()
+    g_host = torch.empty_like(pinned).pin_memory()
+    e2e_n = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_n):
+        p = pinned.to(dev, non_blocking=True)
+        J, g0, gp = gradient(p)
+        g_host.copy_(g0, non_blocking=True)
+        gp_host = gp.cpu()
+        torch.cuda.synchronize()
+    e2e_s = rep.max_over_ranks(time.perf_counter() - t0)
+    if rank == 0:
+        line = {
+            "metric": GRAD_METRIC, "value": value, "unit": GRAD_METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": prec, "data": "synthetic",
+            "config": {"workload": wl, "grid": list(n), "L": L, "scheme": scheme, "dt": dt,
+                       "steps_per_gradient": nsteps, "params": prm,
+                       "objective": "terminal density misfit to a seeded lab-frame target",
+                       "gradients": "psi0, Omega, gamma, c0, c1, c2",
+                       "checkpoints": "ceil(sqrt(steps)) states",
+                       "l2": "L2 flushed (256 MB write) before every timed gradient; "
+                             "the 2.6 MB field is L2-resident within a gradient",
+                       "parallelism": "replicas%d" % world},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "forward_ms": fwd_ms,
+            "adjoint_overhead": (total_ms / args.steps) / fwd_ms,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "bytes_per_launch": 2 * state_bytes,
+                         "avg_launch_ms": dom_avg,
+                         "note": "field L2-resident: a fraction above 1 is L2 bandwidth",
+                         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}},
+            "e2e": {"value": rep.weak_throughput(e2e_n, e2e_s), "unit": GRAD_METRIC,
+                    "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes + 5 * 8, "steps": e2e_n},
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    rep.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# ensemble workload: members on different grids
+# ---------------------------------------------------------------------------
+def run_ens(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2603_25282_gb300 import inputs, sgp
+    from paper_2603_25282_gb300 import build as _build
+    from paper_2603_25282_gb300.replicas import Replicas
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    rep = Replicas("nccl", device=dev)
+    stream = torch.cuda.Stream(device=local_rank)
+    torch.cuda.set_stream(stream)
+    wl = args.workload
+    cfg = ENS_WORKLOADS[wl]
+    members = inputs.ensemble_members(cfg["count"], cfg["seed"] + 1000 * rank)
+    grids = [((m["n"], m["n"]), m["L"]) for m in members]
+    ens = sgp.Ensemble(grids, prec=cfg["prec"], device=local_rank, stream=stream.cuda_stream)
+    keys = ("omega", "gamma", "c0", "c1", "c2", "gx", "gy", "gz")
+    ens.set_params([{k: m[k] for k in keys} for m in members])
+    cdt = np.complex64 if cfg["prec"] == "f32" else np.complex128
+    for i, m in enumerate(members):
+        ens.set_member_state(i, inputs.gaussian_random_phase((m["n"], m["n"]), m["L"], seed=m["seed"],
+                                                             amp=0.01).astype(cdt))
+    pts = sum(m["n"] ** 2 for m in members)
+    sbytes = pts * 5 * (8 if cfg["prec"] == "f32" else 16)
+    ens.step(args.warmup, cfg["dt"], cfg["scheme"])
+    torch.cuda.synchronize()
+    rep.barrier()
+    l0 = ens.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        ev0.record(stream)
+        ens.step(args.steps, cfg["dt"], cfg["scheme"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    rep.barrier()
+    ms = rep.max_over_ranks(ev0.elapsed_time(ev1))
+    launches = ens.launch_count() - l0
+    value = rep.weak_throughput(pts * args.steps, ms * 1e-3)
+    hbm_peak, peak_src = peaks()
+    bpp, bmin = bytes_per_point_step(2, cfg["scheme"], cfg["prec"])
+    gbs = bpp * pts * args.steps / (ms * 1e-3) / 1e9
+    # end to end: one member's state from and to pinned host memory per step
+    # is not the ensemble's use; the e2e number is the whole ensemble's
+    # state set from and read back to host memory around each step
+    host = [torch.from_numpy(inputs.gaussian_random_phase((m["n"], m["n"]), m["L"], seed=m["seed"],
+                                                          amp=0.01).astype(cdt)).pin_memory()
+            for m in members]
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    e2e_n = 2
+    tcur = 0.0                      # the ensemble clock, accumulated as the library does
+    tcur += args.warmup * cfg["dt"]
+    tcur += args.steps * cfg["dt"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_n):
+        for i, h in enumerate(host):
+            ens.set_member_state(i, h, tcur)
+        ens.step(1, cfg["dt"], cfg["scheme"])
+        tcur += 1 * cfg["dt"]
+        for i, o in enumerate(outs):
+            ens.get_member_state(i, o)
+    ens.synchronize()
+    e2e_s = rep.max_over_ranks(time.perf_counter() - t0)
+    if rank == 0:
+        sides = sorted(set(m["n"] for m in members))
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": cfg["prec"], "data": "synthetic",
+            "config": {"workload": wl, "members": cfg["count"], "sides": sides,
+                       "groups": ens.groups, "points_per_step": pts, "scheme": cfg["scheme"],
+                       "dt": cfg["dt"], "field_bytes_per_gpu": sbytes,
+                       "l2": "field %.0f MB > L2 %.0f MB (inputs larger than L2)"
+                             % (sbytes / 1e6, L2_BYTES / 1e6),
+                       "parallelism": "replicas%d" % world},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "roofline": {"bound": "hbm", "kernel": "step (all groups)", "achieved": gbs,
+                         "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "traffic": None,
+                         "bytes_per_point_step": bpp},
+            "e2e": {"value": rep.weak_throughput(pts * e2e_n, e2e_s), "unit": METRIC,
+                    "h2d_bytes_per_step": sbytes, "d2h_bytes_per_step": sbytes, "steps": e2e_n},
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line))
+    ens.close()
     rep.close()
     return 0
 
@@ -368,10 +686,13 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 500; gradients: 5; ensemble: 200)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d512_ts4_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="2d512_ts4_f32",
+                    choices=sorted(WORKLOADS) + sorted(GRAD_WORKLOADS) + sorted(ENS_WORKLOADS))
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
@@ -381,8 +702,15 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.steps is None:
+        args.steps = 5 if args.workload in GRAD_WORKLOADS else (
+            200 if args.workload in ENS_WORKLOADS else 500)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload in GRAD_WORKLOADS:
+        return run_grad(args, rank, world, local_rank)
+    if args.workload in ENS_WORKLOADS:
+        return run_ens(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

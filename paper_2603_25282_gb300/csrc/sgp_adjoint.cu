@@ -72,7 +72,11 @@ __device__ __forceinline__ void apply_spin(const cplx<R> (&v)[5], const SpinRot<
   }
 }
 
-__device__ __forceinline__ void block_sums(double (&acc)[NLA_NT], int nterm, double* out) {
+// Block sums of acc[0..nterm) added to row[slot[k]] (the block's own row of
+// the partials, so no two blocks write the same word and the order of the
+// additions is fixed).
+__device__ __forceinline__ void block_accumulate(double (&acc)[NLA_NT], int nterm, const int4 slot,
+                                                 double* row) {
   __shared__ double red[kAdjThreads / 32][NLA_NT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = 0; k < nterm; ++k) {
@@ -83,7 +87,9 @@ __device__ __forceinline__ void block_sums(double (&acc)[NLA_NT], int nterm, dou
   if (threadIdx.x < nterm) {
     double s = 0.0;
     for (int w = 0; w < kAdjThreads / 32; ++w) s += red[w][threadIdx.x];
-    out[threadIdx.x] = s;
+    const int k = threadIdx.x;
+    const int sl = k == 0 ? slot.x : (k == 1 ? slot.y : (k == 2 ? slot.z : slot.w));
+    row[sl] += s;
   }
 }
 
@@ -99,10 +105,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_nl_adjoint(NLAdjArgs<R> a) {
   typedef cplx<R> C;
   const int m = blockIdx.y;
   const MemberPrm& P = a.mp[m];
-  __shared__ double s_rot[2];
-  if (threadIdx.x == 0) sincos(P.omega * a.t, &s_rot[1], &s_rot[0]);
+  __shared__ double s_rot[3];
+  if (threadIdx.x == 0) {
+    const double t = *a.t_base + a.t_off;
+    sincos(P.omega * t, &s_rot[1], &s_rot[0]);
+    s_rot[2] = t;
+  }
   __syncthreads();
-  const double co = s_rot[0], si = s_rot[1];
+  const double co = s_rot[0], si = s_rot[1], tsub = s_rot[2];
   const R r6 = (R)2.44948974278317809820;
   const R rs5 = (R)0.44721359549995793928;
   const R d = (R)a.delta;
@@ -148,7 +158,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_nl_adjoint(NLAdjArgs<R> a) {
       acc[NLA_C0] += (double)d * (double)rho * ipi;
       acc[NLA_C1] += (double)d * (double)inner5(g, Fpsi).y;
       acc[NLA_C2] += (double)d * (double)cmul(A00, ia).y * (double)rs5;
-      acc[NLA_OMEGA] += (double)d * a.t * dgg * xr * yr * ipi;
+      acc[NLA_OMEGA] += (double)d * tsub * dgg * xr * yr * ipi;
     }
     // tangent v = i g at Phi_out
     C v[5];
@@ -232,7 +242,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_nl_adjoint(NLAdjArgs<R> a) {
       gbase[(size_t)k * a.ntot + id] = cmulmi(v3);
     }
   }
-  block_sums(acc, NLA_NT, a.partials + ((size_t)m * a.nblocks + blockIdx.x) * NLA_NT);
+  block_accumulate(acc, NLA_NT, make_int4(GP_OMEGA, GP_C0, GP_C1, GP_C2),
+                   a.partials + ((size_t)m * a.nblocks + blockIdx.x) * GP_N);
 }
 
 // ----------------------------------------------------------------------------
@@ -256,73 +267,64 @@ __global__ void __launch_bounds__(kAdjThreads) k_lin_param(LinParArgs<R> a) {
     const int iy = (int)((id / a.NX) % a.NY);
     const int ps = ix < a.NX / 2 ? ix : ix - a.NX;
     const int qs = iy < a.NY / 2 ? iy : iy - a.NY;
-    const double nux = kPi * ps / a.Lx, nuy = kPi * qs / a.Ly;
-    double gr[5][2], sr[5][2];
+    C gv[5], sv[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const C gv = gb[(size_t)k * a.ntot + id], sv = sb[(size_t)k * a.ntot + id];
-      gr[k][0] = gv.x; gr[k][1] = gv.y;
-      sr[k][0] = sv.x; sr[k][1] = sv.y;
+      gv[k] = gb[(size_t)k * a.ntot + id];
+      sv[k] = sb[(size_t)k * a.ntot + id];
     }
-    // <g, u> for complex pairs in FP64
-    auto cdot = [&](int i, int j, double* re, double* im) {
-      *re += gr[i][0] * sr[j][0] + gr[i][1] * sr[j][1];
-      *im += gr[i][0] * sr[j][1] - gr[i][1] * sr[j][0];
-    };
-    double ppr = 0, ppi = 0, pmr = 0, pmi = 0, pzr = 0, pzi = 0;
-    {
-      double r, i;
-      r = i = 0; cdot(0, 1, &r, &i); ppr += 2 * r; ppi += 2 * i;
-      r = i = 0; cdot(1, 2, &r, &i); ppr += r6 * r; ppi += r6 * i;
-      r = i = 0; cdot(2, 3, &r, &i); ppr += r6 * r; ppi += r6 * i;
-      r = i = 0; cdot(3, 4, &r, &i); ppr += 2 * r; ppi += 2 * i;
-      r = i = 0; cdot(1, 0, &r, &i); pmr += 2 * r; pmi += 2 * i;
-      r = i = 0; cdot(2, 1, &r, &i); pmr += r6 * r; pmi += r6 * i;
-      r = i = 0; cdot(3, 2, &r, &i); pmr += r6 * r; pmi += r6 * i;
-      r = i = 0; cdot(4, 3, &r, &i); pmr += 2 * r; pmi += 2 * i;
-      const double mz[5] = {2, 1, 0, -1, -2};
-      for (int k = 0; k < 5; ++k) {
-        r = i = 0; cdot(k, k, &r, &i); pzr += mz[k] * r; pzi += mz[k] * i;
-      }
-    }
-    (void)pzr;
+    // P+ = <g, f+ s>, P- = <g, f- s>, Pz = <g, fz s> in the field precision
+    const R r6R = (R)r6;
+    const C Pp = cadd(cscale(cadd(cconjmul(gv[0], sv[1]), cconjmul(gv[3], sv[4])), (R)2),
+                      cscale(cadd(cconjmul(gv[1], sv[2]), cconjmul(gv[2], sv[3])), r6R));
+    const C Pm = cadd(cscale(cadd(cconjmul(gv[1], sv[0]), cconjmul(gv[4], sv[3])), (R)2),
+                      cscale(cadd(cconjmul(gv[2], sv[1]), cconjmul(gv[3], sv[2])), r6R));
+    const C Pz = cadd(cscale(csub(cconjmul(gv[0], sv[0]), cconjmul(gv[4], sv[4])), (R)2),
+                      csub(cconjmul(gv[1], sv[1]), cconjmul(gv[3], sv[3])));
     // Im<g, (w.f) s> = wx Im(P+ + P-)/2 - wy Re(P+ - P-)/2 + wz Im Pz
-    const double kx = 0.5 * (ppi + pmi), ky = -0.5 * (ppr - pmr), kz = pzi;
-    const double ax = a.delta * (-P.gamma * nuy), ay = a.delta * (P.gamma * nux),
-                 az = a.delta * (-P.omega);
-    const double th = sqrt(ax * ax + ay * ay + az * az);
-    double das[2][3] = {{0.0, 0.0, -a.delta}, {-a.delta * nuy, a.delta * nux, 0.0}};
+    const double kx = 0.5 * ((double)Pp.y + (double)Pm.y);
+    const double ky = -0.5 * ((double)Pp.x - (double)Pm.x);
+    const double kz = (double)Pz.y;
+    // w in the field precision (its rounding enters the sum once)
+    const R dR = (R)a.delta, nxR = (R)(kPi / a.Lx) * (R)ps, nyR = (R)(kPi / a.Ly) * (R)qs;
+    const R ax = dR * (-(R)P.gamma * nyR), ay = dR * ((R)P.gamma * nxR), az = dR * (-(R)P.omega);
+    const R th2 = ax * ax + ay * ay + az * az;
+    const R das[2][3] = {{(R)0, (R)0, -dR}, {-dR * nyR, dR * nxR, (R)0}};
+    R sk = (R)1, ck = (R)0, hx = (R)0, hy = (R)0, hz = (R)0;
+    if (th2 > (R)0) {
+      const R th = sqrt(th2);
+      const R ith = (R)1 / th;
+      hx = ax * ith;
+      hy = ay * ith;
+      hz = az * ith;
+      R sh, ch;
+      sincos_r((R)0.5 * th, &sh, &ch);
+      sk = (R)2 * sh * ch * ith;             // sin th / th
+      ck = (R)2 * sh * sh * ith;             // (1 - cos th) / th
+    }
+#pragma unroll
     for (int p = 0; p < 2; ++p) {
-      const double dx = das[p][0], dy = das[p][1], dz = das[p][2];
-      double wx = dx, wy = dy, wz = dz;
-      if (th > 0.0) {
-        const double hx = ax / th, hy = ay / th, hz = az / th;
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        const double sk = sn / th;
-        const double ck = 2.0 * sin(0.5 * th) * sin(0.5 * th) / th;
-        const double fd = hx * dx + hy * dy + hz * dz;
-        const double px = hx * fd, py = hy * fd, pz = hz * fd;
-        wx = px + sk * (dx - px) - ck * (hy * dz - hz * dy);
-        wy = py + sk * (dy - py) - ck * (hz * dx - hx * dz);
-        wz = pz + sk * (dz - pz) - ck * (hx * dy - hy * dx);
-      }
-      acc[p] -= a.scale * (wx * kx + wy * ky + wz * kz);
+      const R dx = das[p][0], dy = das[p][1], dz = das[p][2];
+      const R fd = hx * dx + hy * dy + hz * dz;
+      const R px = hx * fd, py = hy * fd, pz = hz * fd;
+      const R wx = px + sk * (dx - px) - ck * (hy * dz - hz * dy);
+      const R wy = py + sk * (dy - py) - ck * (hz * dx - hx * dz);
+      const R wz = pz + sk * (dz - pz) - ck * (hx * dy - hy * dx);
+      acc[p] -= a.scale * ((double)wx * kx + (double)wy * ky + (double)wz * kz);
     }
   }
-  block_sums(acc, LPA_NT, a.partials + ((size_t)m * a.nblocks + blockIdx.x) * LPA_NT);
+  block_accumulate(acc, LPA_NT, make_int4(GP_OMEGA, GP_GAMMA, 0, 0),
+                   a.partials + ((size_t)m * a.nblocks + blockIdx.x) * GP_N);
 }
 
-__global__ void k_accum_params(const double* part, int nblocks, int nterm, int members,
-                               int4 slots, double* dp) {
+__global__ void k_reduce_params(const double* part, int nblocks, int members, double* dp) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= members * nterm) return;
-  const int m = id / nterm, k = id - m * nterm;
-  const double* p = part + (size_t)m * nblocks * nterm + k;
+  if (id >= members * GP_N) return;
+  const int m = id / GP_N, k = id - m * GP_N;
+  const double* p = part + (size_t)m * nblocks * GP_N + k;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += p[(size_t)b * nterm];
-  const int slot = k == 0 ? slots.x : (k == 1 ? slots.y : (k == 2 ? slots.z : slots.w));
-  dp[(size_t)m * GP_N + slot] += s;
+  for (int b = 0; b < nblocks; ++b) s += p[(size_t)b * GP_N];
+  dp[id] = s;
 }
 
 }  // namespace
@@ -341,12 +343,10 @@ cudaError_t launch_lin_param(const LinParArgs<R>& a, int members, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_accum_params(const double* part, int nblocks, int nterm, int members,
-                                const int* slots, double* dp, cudaStream_t s) {
-  const int4 sl = make_int4(slots[0], nterm > 1 ? slots[1] : 0, nterm > 2 ? slots[2] : 0,
-                            nterm > 3 ? slots[3] : 0);
-  const int n = members * nterm;
-  k_accum_params<<<(n + 127) / 128, 128, 0, s>>>(part, nblocks, nterm, members, sl, dp);
+cudaError_t launch_reduce_params(const double* part, int nblocks, int members, double* dp,
+                                 cudaStream_t s) {
+  const int n = members * GP_N;
+  k_reduce_params<<<(n + 127) / 128, 128, 0, s>>>(part, nblocks, members, dp);
   return cudaGetLastError();
 }
 

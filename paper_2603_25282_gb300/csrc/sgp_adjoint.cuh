@@ -39,9 +39,10 @@ struct NLAdjArgs {
   int nx, ny;
   double x0, hx, y0, hy, z0, hz;
   double delta;             // forward substep size
-  double t;                 // time of the substep (absolute)
+  const double* t_base;     // the substep's time is *t_base + t_off (FP64, on the device)
+  double t_off;
   const MemberPrm* mp;
-  double* partials;         // [member][nblocks][NLA_NT]
+  double* partials;         // [member][nblocks][GP_N], each block adds to its own row
   int nblocks;
 };
 
@@ -55,7 +56,7 @@ struct LinParArgs {
   double delta;
   double scale;             // 1/(NX NY [NZ])
   const MemberPrm* mp;
-  double* partials;         // [member][nblocks][LPA_NT]
+  double* partials;         // [member][nblocks][GP_N], as NLAdjArgs
   int nblocks;
 };
 
@@ -71,8 +72,8 @@ template <typename R>
 cudaError_t launch_nl_adjoint(const NLAdjArgs<R>& a, int members, cudaStream_t s);
 template <typename R>
 cudaError_t launch_lin_param(const LinParArgs<R>& a, int members, cudaStream_t s);
-// dp[m][slot[k]] += sum over blocks of part[m][b][k], k < nterm
-cudaError_t launch_accum_params(const double* part, int nblocks, int nterm, int members,
-                                const int* slots, double* dp, cudaStream_t s);
+// dp[m][k] = sum over blocks of part[m][b][k], k < GP_N (fixed order)
+cudaError_t launch_reduce_params(const double* part, int nblocks, int members, double* dp,
+                                 cudaStream_t s);
 
 }  // namespace sgp

@@ -221,8 +221,14 @@ struct AdjRec {
   size_t spec_cap = 0;
   double* dp = nullptr;            // [batch][GP_N]
   size_t dp_cap = 0;
-  double* part = nullptr;          // per-block partial sums
+  double* part = nullptr;          // per-block partial sums [batch][blocks][GP_N]
   size_t part_cap = 0;
+  // captured full-length segment and what it was captured for
+  cudaGraphExec_t graph = nullptr;
+  long long graph_len = 0, graph_launches = 0;
+  double graph_dt = 0.0;
+  int graph_scheme = -1;
+  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 }  // namespace
@@ -351,6 +357,10 @@ void free_graphs(sgp_ctx* c) {
 }
 
 void free_tables(sgp_ctx* c) {
+  if (c->adj.graph) {            // the captured adjoint segment points at the tables
+    cudaGraphExecDestroy(c->adj.graph);
+    c->adj.graph = nullptr;
+  }
   for (auto& t : c->tables) {
     cudaFree(t.mt);
     cudaFree(t.kz);
@@ -652,6 +662,7 @@ sgp_status ensure_buf(sgp_ctx* c, void** p, size_t* cap, size_t bytes) {
 
 void free_adj(sgp_ctx* c) {
   AdjRec& r = c->adj;
+  if (r.graph) cudaGraphExecDestroy(r.graph);
   cudaFree(r.ckpt);
   cudaFree(r.seg);
   cudaFree(r.g);
@@ -697,16 +708,10 @@ sgp_status to_spectral(sgp_ctx* c, void* f) {
   return SGP_OK;
 }
 
-sgp_status accum(sgp_ctx* c, int nblocks, int nterm, const int* slots) {
-  c->launches++;
-  SGP_CUDA(c, launch_accum_params(c->adj.part, nblocks, nterm, c->batch, slots, c->adj.dp,
-                                  c->stream));
-  return SGP_OK;
-}
-
-// g <- (D N_d(Phi_in))^T g at Phi_out = phi, and the parameter terms
+// g <- (D N_d(Phi_in))^T g at Phi_out = phi, plus the parameter terms (added
+// to the per-block partials)
 template <typename R>
-sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t) {
+sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t_off) {
   NLAdjArgs<R> a{};
   a.g = (cplx<R>*)c->adj.g;
   a.phi = (const cplx<R>*)phi;
@@ -720,17 +725,15 @@ sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t
   a.z0 = c->dim == 3 ? -c->L[2] : 0.0;
   a.hz = c->dim == 3 ? c->h[2] : 0.0;
   a.delta = delta;
-  a.t = t;
+  a.t_base = c->t_dev;
+  a.t_off = t_off;
   a.mp = c->mp_dev;
   a.partials = c->adj.part;
   a.nblocks = adjoint_blocks(c->ntot);
   c->launches++;
-  {
-    ProfScope ps(c, PK_OTHER);
-    SGP_CUDA(c, launch_nl_adjoint<R>(a, c->batch, c->stream));
-  }
-  const int slots[4] = {GP_OMEGA, GP_C0, GP_C1, GP_C2};
-  return accum(c, a.nblocks, NLA_NT, slots);
+  ProfScope ps(c, PK_OTHER);
+  SGP_CUDA(c, launch_nl_adjoint<R>(a, c->batch, c->stream));
+  return SGP_OK;
 }
 
 // g <- L(-d) g, and the Omega and gamma terms from the transforms of g and
@@ -759,8 +762,6 @@ sgp_status adjoint_linear(sgp_ctx* c, const void* phi, double delta) {
     ProfScope ps(c, PK_OTHER);
     SGP_CUDA(c, launch_lin_param<R>(a, c->batch, c->stream));
   }
-  const int slots[2] = {GP_OMEGA, GP_GAMMA};
-  SGP_TRY(accum(c, a.nblocks, LPA_NT, slots));
   // the linear flow over -delta on the transformed g, then back to space
   const LinTables* t = nullptr;
   SGP_TRY(get_tables<R>(c, -delta, &t));
@@ -779,9 +780,107 @@ struct SubRec {
   double toff;     // time of the substep relative to the segment start
 };
 
+// Substeps of n steps of the scheme from a segment start, with the
+// nonlinear substeps that meet at a step boundary merged (same time; the
+// flow of Eq. (solution2) over a then b is the flow over a + b).  The time
+// of the substep at the end of step s is (s + 1) dt, as in the step path.
+std::vector<SubRec> segment_substeps(int scheme, long long n, double dt) {
+  const auto seq = scheme_seq(scheme);
+  std::vector<SubRec> subs;
+  for (long long s = 0; s < n; ++s) {
+    double sub = 0.0;
+    for (size_t k = 0; k < seq.size(); ++k) {
+      const double delta = seq[k].second * dt;
+      if (seq[k].first == 'L') {
+        subs.push_back({'L', delta, (double)s * dt + sub * dt});
+        sub += seq[k].second;
+        continue;
+      }
+      const double toff = (k == seq.size() - 1) ? (double)(s + 1) * dt
+                                                  : (double)s * dt + sub * dt;
+      if (k == 0 && !subs.empty() && subs.back().kind == 'N')
+        subs.back().delta += delta;        // meets the previous step's last N
+      else
+        subs.push_back({'N', delta, toff});
+    }
+  }
+  return subs;
+}
+
+// One segment: recompute the states from seg[0] substep by substep, then
+// carry g back through the substeps in reverse order.  Reads the segment
+// start time from the device clock.
+template <typename R>
+sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs) {
+  AdjRec& r = c->adj;
+  const size_t sb = state_bytes(c);
+  char* seg = (char*)r.seg;
+  for (size_t j = 0; j < subs.size(); ++j) {
+    void* out = seg + sb * (j + 1);
+    SGP_CUDA(c, cudaMemcpyAsync(out, seg + sb * j, sb, cudaMemcpyDeviceToDevice, c->stream));
+    if (subs[j].kind == 'N') {
+      SGP_TRY(x_pass_on<R>(c, out, XP_NL, subs[j].delta, subs[j].toff));
+    } else {
+      SGP_TRY(x_pass_on<R>(c, out, XP_FWD, 0.0, 0.0));
+      SGP_TRY(linear_middle_on<R>(c, out, subs[j].delta));
+      SGP_TRY(x_pass_on<R>(c, out, XP_INV, 0.0, 0.0));
+    }
+  }
+  for (size_t j = subs.size(); j-- > 0;) {
+    const void* phi_out = seg + sb * (j + 1);
+    if (subs[j].kind == 'N')
+      SGP_TRY(adjoint_nonlinear<R>(c, phi_out, subs[j].delta, subs[j].toff));
+    else
+      SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta));
+  }
+  return SGP_OK;
+}
+
+void free_adj_graph(sgp_ctx* c) {
+  if (c->adj.graph) cudaGraphExecDestroy(c->adj.graph);
+  c->adj.graph = nullptr;
+}
+
+// Captured full-length segment (cached; rebuilt when the run, the buffers or
+// the tables change).
+template <typename R>
+sgp_status segment_graph(sgp_ctx* c, const std::vector<SubRec>& subs, cudaGraphExec_t* out) {
+  AdjRec& r = c->adj;
+  const void* key[5] = {r.seg, r.g, r.spec, r.part, c->t_dev};
+  if (r.graph && r.graph_len == r.interval && r.graph_dt == r.dt &&
+      r.graph_scheme == r.scheme && std::memcmp(key, r.graph_key, sizeof key) == 0) {
+    *out = r.graph;
+    return SGP_OK;
+  }
+  free_adj_graph(c);
+  const long long launches0 = c->launches;
+  SGP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  sgp_status st = emit_segment<R>(c, subs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  r.graph_launches = c->launches - launches0;
+  c->launches = launches0;
+  if (st != SGP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, SGP_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c, SGP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  r.graph = exec;
+  r.graph_len = r.interval;
+  r.graph_dt = r.dt;
+  r.graph_scheme = r.scheme;
+  std::memcpy(r.graph_key, key, sizeof key);
+  *out = exec;
+  return SGP_OK;
+}
+
 // Backward sweep over the recorded trajectory: each segment is recomputed
-// from its checkpoint substep by substep (unmerged), then g is carried back
-// through the segment's substeps in reverse order.
+// from its checkpoint, then g is carried back through its substeps in
+// reverse order.  Full-length segments replay one captured graph.
 template <typename R>
 sgp_status backward_sweep(sgp_ctx* c) {
   AdjRec& r = c->adj;
@@ -790,54 +889,37 @@ sgp_status backward_sweep(sgp_ctx* c) {
   const size_t per_seg = (size_t)r.interval * seq.size() + 1;
   SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, sb * per_seg));
   SGP_TRY(ensure_buf(c, &r.spec, &r.spec_cap, sb));
-  const size_t need_part = (size_t)c->batch * adjoint_blocks(c->ntot) * NLA_NT * sizeof(double);
-  SGP_TRY(ensure_buf(c, (void**)&r.part, &r.part_cap, need_part));
+  const int nblocks = adjoint_blocks(c->ntot);
+  const size_t part_bytes = (size_t)c->batch * nblocks * GP_N * sizeof(double);
+  SGP_TRY(ensure_buf(c, (void**)&r.part, &r.part_cap, part_bytes));
+  SGP_CUDA(c, cudaMemsetAsync(r.part, 0, part_bytes, c->stream));
   for (const auto& st : seq)
     if (st.first == 'L') {
       const LinTables* t = nullptr;
       SGP_TRY(get_tables<R>(c, st.second * r.dt, &t));
       SGP_TRY(get_tables<R>(c, -st.second * r.dt, &t));
     }
-  std::vector<SubRec> subs;
+  const std::vector<SubRec> full = segment_substeps(r.scheme, r.interval, r.dt);
+  const bool graphs = c->use_graphs && !c->profiling;
   for (long long k = r.nck - 1; k >= 0; --k) {
     const long long n = std::min(r.interval, r.nsteps - k * r.interval);
     const double tk = r.t0 + (double)(k * r.interval) * r.dt;
     c->launches++;
     k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, tk);
     SGP_CUDA(c, cudaGetLastError());
-    char* seg = (char*)r.seg;
-    SGP_CUDA(c, cudaMemcpyAsync(seg, (const char*)r.ckpt + sb * (size_t)k, sb,
+    SGP_CUDA(c, cudaMemcpyAsync(r.seg, (const char*)r.ckpt + sb * (size_t)k, sb,
                                 cudaMemcpyDeviceToDevice, c->stream));
-    subs.clear();
-    double toff = 0.0;
-    for (long long s = 0; s < n; ++s) {
-      const double tstep = (double)s * r.dt;
-      double sub = 0.0;
-      for (const auto& st : seq) {
-        const size_t j = subs.size();
-        void* out = seg + sb * (j + 1);
-        SGP_CUDA(c, cudaMemcpyAsync(out, seg + sb * j, sb, cudaMemcpyDeviceToDevice, c->stream));
-        const double delta = st.second * r.dt;
-        toff = tstep + sub * r.dt;
-        if (st.first == 'N') {
-          SGP_TRY(x_pass_on<R>(c, out, XP_NL, delta, toff));
-        } else {
-          SGP_TRY(x_pass_on<R>(c, out, XP_FWD, 0.0, 0.0));
-          SGP_TRY(linear_middle_on<R>(c, out, delta));
-          SGP_TRY(x_pass_on<R>(c, out, XP_INV, 0.0, 0.0));
-          sub += st.second;
-        }
-        subs.push_back({st.first, delta, toff});
-      }
-    }
-    for (size_t j = subs.size(); j-- > 0;) {
-      const void* phi_out = seg + sb * (j + 1);
-      if (subs[j].kind == 'N')
-        SGP_TRY(adjoint_nonlinear<R>(c, phi_out, subs[j].delta, tk + subs[j].toff));
-      else
-        SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta));
+    if (n == r.interval && graphs && r.nck > 1) {
+      cudaGraphExec_t exec = nullptr;
+      SGP_TRY(segment_graph<R>(c, full, &exec));
+      SGP_CUDA(c, cudaGraphLaunch(exec, c->stream));
+      c->launches += r.graph_launches;
+    } else {
+      SGP_TRY(emit_segment<R>(c, n == r.interval ? full : segment_substeps(r.scheme, n, r.dt)));
     }
   }
+  c->launches++;
+  SGP_CUDA(c, launch_reduce_params(r.part, nblocks, c->batch, r.dp, c->stream));
   return SGP_OK;
 }
 

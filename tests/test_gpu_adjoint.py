@@ -107,6 +107,26 @@ def test_adjoint_fp64_3d_matches_oracle_fd():
         assert abs(dp[k] - fd_par[name]) <= 1e-6 * scale, name
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_backward_graph_replay_equals_eager(prec):
+    n, L, dt, nsteps = (32, 32), 8.0, 1e-3, 30
+    psi0 = inputs.gaussian_random_phase(n, L, seed=51, amp=0.3)
+    dtype = np.complex64 if prec == "f32" else np.complex128
+    rng = np.random.default_rng(52)
+    gT = (rng.standard_normal((1, 5) + n) + 1j * rng.standard_normal((1, 5) + n)).astype(dtype)
+    out = []
+    for graphs in (True, False):
+        ctx = sgp.Context(n, L, prec=prec)
+        ctx.set_graphs(graphs)
+        ctx.set_params(**dataclasses.asdict(PRM_SMALL))
+        ctx.set_state(psi0.astype(dtype)[None].copy(), 0.0)
+        ctx.record(nsteps, dt, "ts2", 4)          # 8 segments, the first one ragged
+        out.append(ctx.backward(gT))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_adjoint_global_phase_invariance():
     n, L = (32, 32), 8.0
     psi0 = inputs.gaussian_random_phase(n, L, seed=31, amp=0.3)
