@@ -291,6 +291,10 @@ def run_ours(args, rank, world, local_rank):
 
     max_over_ranks = rep.max_over_ranks
 
+    # ---- kernel variants chosen by the autotuner (untimed) -----------------
+    ctx.set_state(dev_init, 0.0)
+    plan, tune_ms = ([0, 0, 0], None) if args.no_tune else ctx.autotune(reps=10, timings=True)
+
     # ---- device-resident timing -------------------------------------------
     ctx.set_state(dev_init, 0.0)
     ctx.step(args.warmup, dt, scheme)
@@ -367,7 +371,8 @@ def run_ours(args, rank, world, local_rank):
                        "field_bytes_per_gpu": state_bytes,
                        "l2": "field %.0f MB > L2 %.0f MB (inputs larger than L2)"
                              % (state_bytes / 1e6, L2_BYTES / 1e6),
-                       "parallelism": "replicas%d" % world},
+                       "parallelism": "replicas%d" % world,
+                       "plan": plan, "tune_ms": tune_ms},
             "gpu_launches": launches,
             "clocks": clocks,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
@@ -478,6 +483,10 @@ def run_grad(args, rank, world, local_rank):
     prm_vec = [prm[k] for k in ("omega", "gamma", "c0", "c1", "c2")]
     psi_dev = torch.from_numpy(host).to(dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    ctx.set_params_batch([dict(zip(("omega", "gamma", "c0", "c1", "c2"), prm_vec),
+                               gx=trap[0], gy=trap[1], gz=trap[2])])
+    ctx.set_state(psi_dev, 0.0)
+    plan = [0, 0, 0] if args.no_tune else ctx.autotune(reps=20)
 
     def gradient(psi0):
         p0 = psi0.detach().clone().requires_grad_(True)
@@ -559,7 +568,7 @@ def run_grad(args, rank, world, local_rank):
                        "steps_per_gradient": nsteps, "params": prm,
                        "objective": "terminal density misfit to a seeded lab-frame target",
                        "gradients": "psi0, Omega, gamma, c0, c1, c2",
-                       "checkpoints": "ceil(sqrt(steps)) states",
+                       "checkpoints": "ceil(sqrt(steps)) states", "plan": plan,
                        "l2": "L2 flushed (256 MB write) before every timed gradient; "
                              "the 2.6 MB field is L2-resident within a gradient",
                        "parallelism": "replicas%d" % world},
@@ -614,6 +623,8 @@ def run_ens(args, rank, world, local_rank):
                                                              amp=0.01).astype(cdt))
     pts = sum(m["n"] ** 2 for m in members)
     sbytes = pts * 5 * (8 if cfg["prec"] == "f32" else 16)
+    if not args.no_tune:
+        ens.autotune(reps=10)
     ens.step(args.warmup, cfg["dt"], cfg["scheme"])
     torch.cuda.synchronize()
     rep.barrier()
@@ -693,6 +704,7 @@ def main():
     ap.add_argument("--workload", default="2d512_ts4_f32",
                     choices=sorted(WORKLOADS) + sorted(GRAD_WORKLOADS) + sorted(ENS_WORKLOADS))
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default kernel variants, no autotuner")
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")

@@ -66,6 +66,9 @@ typedef enum { SGP_F32 = 32, SGP_F64 = 64 } sgp_prec;
  * the a_j and the linear flow the b_j.  Time advances in the L substeps. */
 typedef enum { SGP_TS2 = 0, SGP_TS4 = 1 } sgp_scheme;
 
+/* Flags of sgp_autotune. */
+enum { SGP_TUNE_FORCE = 1 };
+
 /* Substep kinds for sgp_substep. */
 typedef enum { SGP_SUB_NONLINEAR = 0, SGP_SUB_LINEAR = 1 } sgp_substep_kind;
 
@@ -159,6 +162,40 @@ sgp_status sgp_step(sgp_ctx* ctx, long long nsteps, double dt, int scheme);
 /* Enable (default) or disable graph replay in sgp_step. */
 sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
 
+/* ---------------------------------------------------------------------
+ * Kernel variants (FFT tile and radix schedules) and the autotuner.
+ * Every pass kernel exists in up to four variants per line length N:
+ *   0  default: x-pass CTAs of about 256 threads (rows side by side), line
+ *      pass up to 512 threads with TILE >= 4 (FP32) / 2 (FP64) columns;
+ *   1  CTAs of about half the threads (line pass TILE down to 1);
+ *   2  CTAs of about a quarter of the threads;
+ *   3  FP32 and N a power of two only: radix-4 plan (4 elements per thread
+ *      instead of 8).
+ * A plan is one variant per axis (x-pass, y lines, z lines).  Variants
+ * compute the same transforms with different rounding (variant 3 has a
+ * different radix plan), so results agree to rounding, not bit for bit.
+ * ------------------------------------------------------------------- */
+/* 1 if variant v exists for line length n at precision prec, else 0. */
+int sgp_variant_exists(int prec, int n, int variant);
+/* Set the plan: variants[a] for axis a < dim.  Synchronises the context
+ * stream; drops captured graphs.  SGP_EINVAL for a variant that does not
+ * exist (nothing is changed then). */
+sgp_status sgp_set_plan(sgp_ctx* ctx, const int* variants);
+/* Current plan into variants[0..2] (0 for absent axes). */
+sgp_status sgp_get_plan(const sgp_ctx* ctx, int* variants);
+/* Autotuner: axis by axis (the other axes at their current variant), run
+ * `reps` Strang steps (1..1000) of dt = 1e-3 with each variant of that
+ * axis on a scratch copy of the field, after one warm-up step, timed with
+ * CUDA events on the context stream; keep the fastest (a higher-numbered
+ * variant must be at least 1.5% faster to replace a lower one).  The state
+ * and the time are not changed.  Results are cached per process by
+ * (device, precision, grid, batch); a cached plan is reused unless flags
+ * has SGP_TUNE_FORCE or ms_out is given.  ms_out (may be NULL): 3 x 4
+ * doubles, ms per step of [axis][variant], -1 where the variant or axis
+ * does not exist.  Synchronises.  Allocates one field-sized scratch buffer
+ * for the duration of the call. */
+sgp_status sgp_autotune(sgp_ctx* ctx, int reps, int flags, double* ms_out);
+
 /* Apply one substep of size delta (delta may be negative, Sec. 3.3 TS4):
  * SGP_SUB_NONLINEAR applies the exact flow (solution2) at the current time;
  * SGP_SUB_LINEAR applies the exact flow (sl1) and advances the time by delta.
@@ -229,6 +266,9 @@ sgp_status sgp_ensemble_get_member_state(sgp_ens* ens, int member, void* dst,
 sgp_status sgp_ensemble_step(sgp_ens* ens, long long nsteps, double dt, int scheme);
 /* Observables of every member into out[0..count-1] (synchronises). */
 sgp_status sgp_ensemble_observables(sgp_ens* ens, sgp_obs* out);
+/* sgp_autotune for every grid group of the ensemble (flags as there);
+ * drops the ensemble's captured graphs. */
+sgp_status sgp_ensemble_autotune(sgp_ens* ens, int reps, int flags);
 sgp_status sgp_ensemble_synchronize(sgp_ens* ens);
 long long sgp_ensemble_launch_count(const sgp_ens* ens);
 const char* sgp_ensemble_last_error(const sgp_ens* ens);

@@ -24,12 +24,12 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.
 
 # (object name, source, extra defines)
 UNITS = [
-    ("inst_f32_x", "sgp_inst.cu", ["-DSGP_REAL=float", "-DSGP_PART=0"]),
-    ("inst_f32_l", "sgp_inst.cu", ["-DSGP_REAL=float", "-DSGP_PART=1"]),
-    ("inst_f64_x", "sgp_inst.cu", ["-DSGP_REAL=double", "-DSGP_PART=0"]),
-    ("inst_f64_l", "sgp_inst.cu", ["-DSGP_REAL=double", "-DSGP_PART=1"]),
-    ("adjoint", "sgp_adjoint.cu", []),
     ("api", "sgp_api.cu", []),
+    ("adjoint", "sgp_adjoint.cu", []),
+] + [
+    ("inst_%s_%s_v%d" % (r[0:3], "xl"[part], v), "sgp_inst.cu",
+     ["-DSGP_REAL=%s" % r, "-DSGP_PART=%d" % part, "-DSGP_VAR=%d" % v])
+    for r, nv in (("float", 4), ("double", 3)) for part in (0, 1) for v in range(nv)
 ]
 
 

@@ -246,7 +246,9 @@ struct sgp_ctx {
   long long ntot = 0;
   size_t elem = 8;
   void* field = nullptr;
-  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* tw[3] = {nullptr, nullptr, nullptr};     // twiddles of the default radix plan per axis
+  void* tw4[3] = {nullptr, nullptr, nullptr};    // FP32 radix-4 plan (variant 3), on demand
+  int var[3] = {0, 0, 0};                        // kernel variant per axis (x-pass, y, z lines)
   double* t_dev = nullptr;
   double t = 0.0;
   std::vector<sgp_params> prm;      // per member
@@ -425,7 +427,7 @@ template <typename R>
 sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
   XPassArgs<R> a{};
   a.field = (cplx<R>*)field;
-  a.tw = (const TwE<R>*)c->tw[0];
+  a.tw = (const TwE<R>*)(c->var[0] == 3 ? c->tw4[0] : c->tw[0]);
   a.ntot = c->ntot;
   a.rows = c->n[1] * c->n[2];
   a.ny = c->n[1];
@@ -442,7 +444,7 @@ sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_o
   a.t_off = t_off;
   c->launches++;
   ProfScope ps(c, PK_X);
-  SGP_CUDA(c, launch_xpass<R>(c->n[0], a, c->batch, c->stream));
+  SGP_CUDA(c, launch_xpass<R>(c->n[0], c->var[0], a, c->batch, c->stream));
   return SGP_OK;
 }
 
@@ -456,7 +458,7 @@ template <typename R>
 sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTables* t) {
   LPassArgs<R> a{};
   a.field = (cplx<R>*)field;
-  a.tw = (const TwE<R>*)c->tw[axis];
+  a.tw = (const TwE<R>*)(c->var[axis] == 3 ? c->tw4[axis] : c->tw[axis]);
   a.ntot = c->ntot;
   a.nx = c->n[0];
   const long long nxy = (long long)c->n[0] * c->n[1];
@@ -486,7 +488,7 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
   }
   c->launches++;
   ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
-  SGP_CUDA(c, launch_linepass<R>(c->n[axis], a, planes, c->batch, c->stream));
+  SGP_CUDA(c, launch_linepass<R>(c->n[axis], c->var[axis], a, planes, c->batch, c->stream));
   return SGP_OK;
 }
 
@@ -924,6 +926,120 @@ sgp_status backward_sweep(sgp_ctx* c) {
 }
 
 // ----------------------------------------------------------------------------
+// kernel variants: plan and autotuner
+// ----------------------------------------------------------------------------
+void drop_graphs(sgp_ctx* c) {
+  free_graphs(c);
+  if (c->adj.graph) {
+    cudaGraphExecDestroy(c->adj.graph);
+    c->adj.graph = nullptr;
+  }
+}
+
+// Switch axis `a` to variant v: twiddles of its radix plan, kernel
+// attributes; captured graphs are dropped (they embed the old kernels).
+sgp_status use_variant(sgp_ctx* c, int a, int v) {
+  const int pb = c->prec == SGP_F32 ? 4 : 8;
+  if (!variant_exists(pb, c->n[a], v))
+    return fail(c, SGP_EINVAL, "variant %d does not exist for N = %d on axis %d", v, c->n[a], a);
+  if (v == 3 && !c->tw4[a]) {
+    SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+    SGP_CUDA(c, cudaMalloc(&c->tw4[a], (size_t)c->n[a] * sizeof(TwE<float>)));
+    k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], 4, (TwE<float>*)c->tw4[a]);
+    c->launches++;
+    SGP_CUDA(c, cudaGetLastError());
+  }
+  cudaError_t e = c->prec == SGP_F32
+                      ? (a == 0 ? prepare_xpass<float>(c->n[a], v) : prepare_linepass<float>(c->n[a], v))
+                      : (a == 0 ? prepare_xpass<double>(c->n[a], v) : prepare_linepass<double>(c->n[a], v));
+  if (e != cudaSuccess) return fail(c, SGP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  if (c->var[a] != v) {
+    SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    c->var[a] = v;
+  }
+  return SGP_OK;
+}
+
+// process-wide results of the autotuner, keyed by device, precision, grid
+// and batch
+std::map<std::string, std::vector<int>>& tune_cache() {
+  static std::map<std::string, std::vector<int>> m;
+  return m;
+}
+
+std::string tune_key(const sgp_ctx* c) {
+  char b[160];
+  snprintf(b, sizeof b, "%d:%d:%d:%d:%d:%d:%d", c->device, c->prec, c->dim, c->n[0], c->n[1],
+           c->n[2], c->batch);
+  return b;
+}
+
+// Times the variants axis by axis (coordinate descent: axis a's variants
+// with the other axes at their current choice) by running `reps` TS2 steps
+// of dt = 1e-3 on a scratch copy of the field with CUDA events after one
+// warm-up step: the data stay a physical state, so the nonlinear flow takes
+// its usual branches, and the pass interplay of a real step is included.  A
+// variant replaces an earlier (lower-numbered) one only when it is at least
+// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][4]:
+// ms per step with that variant (-1 where a variant does not exist or the
+// axis is absent).
+template <typename R>
+sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
+  const size_t sb = state_bytes(c);
+  void* scratch = nullptr;
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  SGP_CUDA(c, cudaMalloc(&scratch, sb));
+  SGP_CUDA(c, cudaMemcpyAsync(scratch, c->field, sb, cudaMemcpyDeviceToDevice, c->stream));
+  std::swap(c->field, scratch);            // the steps below advance the copy
+  const double dt = 1e-3;
+  sgp_status st = ensure_tables<R>(c, dt, SGP_TS2);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int pb = sizeof(R);
+  int best[3] = {c->var[0], c->var[1], c->var[2]};
+  if (ms_out)
+    for (int k = 0; k < 3 * kVariants; ++k) ms_out[k] = -1.0;
+  for (int a = 0; a < c->dim && st == SGP_OK; ++a) {
+    double best_ms = -1.0;
+    for (int v = 0; v < kVariants && st == SGP_OK; ++v) {
+      if (!variant_exists(pb, c->n[a], v)) continue;
+      st = use_variant(c, a, v);
+      if (st != SGP_OK) break;
+      c->launches++;
+      k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, c->t);
+      st = emit_steps<R>(c, 1, dt, SGP_TS2);
+      if (st != SGP_OK) break;
+      cudaEventRecord(e0, c->stream);
+      st = emit_steps<R>(c, reps, dt, SGP_TS2);
+      cudaEventRecord(e1, c->stream);
+      if (st != SGP_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = fail(c, SGP_ECUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double avg = ms / reps;
+      if (ms_out) ms_out[a * kVariants + v] = avg;
+      if (best_ms < 0.0 || avg < 0.985 * best_ms) {
+        best_ms = avg;
+        best[a] = v;
+      }
+    }
+    if (st == SGP_OK) st = use_variant(c, a, best[a]);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(c->stream);
+  std::swap(c->field, scratch);
+  cudaFree(scratch);
+  if (st == SGP_OK) tune_cache()[tune_key(c)] = std::vector<int>(best, best + 3);
+  return st;
+}
+
+// ----------------------------------------------------------------------------
 // observables
 // ----------------------------------------------------------------------------
 void assemble_obs(const double* s, int dim, double cell, double t, const sgp_params& p,
@@ -1283,6 +1399,45 @@ sgp_status sgp_set_graphs(sgp_ctx* c, int enable) {
   return SGP_OK;
 }
 
+int sgp_variant_exists(int prec, int n, int variant) {
+  if (prec != SGP_F32 && prec != SGP_F64) return 0;
+  return variant_exists(prec == SGP_F32 ? 4 : 8, n, variant) ? 1 : 0;
+}
+
+sgp_status sgp_set_plan(sgp_ctx* c, const int* variants) {
+  if (!c) return SGP_EINVAL;
+  if (!variants) return fail(c, SGP_EINVAL, "NULL variants");
+  const int pb = c->prec == SGP_F32 ? 4 : 8;
+  for (int a = 0; a < c->dim; ++a)
+    if (!variant_exists(pb, c->n[a], variants[a]))
+      return fail(c, SGP_EINVAL, "variant %d does not exist for N = %d on axis %d", variants[a],
+                  c->n[a], a);
+  DeviceGuard guard(c->device);
+  for (int a = 0; a < c->dim; ++a) SGP_TRY(use_variant(c, a, variants[a]));
+  return SGP_OK;
+}
+
+sgp_status sgp_get_plan(const sgp_ctx* c, int* variants) {
+  if (!c || !variants) return SGP_EINVAL;
+  for (int a = 0; a < 3; ++a) variants[a] = a < c->dim ? c->var[a] : 0;
+  return SGP_OK;
+}
+
+sgp_status sgp_autotune(sgp_ctx* c, int reps, int flags, double* ms_out) {
+  if (!c) return SGP_EINVAL;
+  if (reps < 1 || reps > 1000) return fail(c, SGP_EINVAL, "reps must be in [1, 1000]");
+  DeviceGuard guard(c->device);
+  if (!(flags & SGP_TUNE_FORCE) && !ms_out) {
+    auto it = tune_cache().find(tune_key(c));
+    if (it != tune_cache().end()) {
+      for (int a = 0; a < c->dim; ++a) SGP_TRY(use_variant(c, a, it->second[a]));
+      return SGP_OK;
+    }
+  }
+  return c->prec == SGP_F32 ? autotune_impl<float>(c, reps, ms_out)
+                            : autotune_impl<double>(c, reps, ms_out);
+}
+
 sgp_status sgp_substep(sgp_ctx* c, int kind, double delta) {
   if (!c) return SGP_EINVAL;
   if (kind != SGP_SUB_NONLINEAR && kind != SGP_SUB_LINEAR)
@@ -1355,6 +1510,7 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   free_adj(c);
   cudaFree(c->field);
   for (void* t : c->tw) cudaFree(t);
+  for (void* t : c->tw4) cudaFree(t);
   cudaFree(c->t_dev);
   cudaFree(c->mp_dev);
   cudaFree(c->partials);
@@ -1667,6 +1823,17 @@ sgp_status sgp_ensemble_observables(sgp_ens* e, sgp_obs* out) {
     for (int m = 0; m < e->count; ++m)
       if (e->member_group[m] == (int)g) out[m] = tmp[e->member_index[m]];
   }
+  return SGP_OK;
+}
+
+sgp_status sgp_ensemble_autotune(sgp_ens* e, int reps, int flags) {
+  if (!e) return SGP_EINVAL;
+  DeviceGuard guard(e->device);
+  for (sgp_ctx* g : e->groups) {
+    sgp_status st = sgp_autotune(g, reps, flags, nullptr);
+    if (st != SGP_OK) return efail(e, st, "%s", g->err.c_str());
+  }
+  ens_free_graphs(e);
   return SGP_OK;
 }
 

@@ -149,13 +149,25 @@ template <typename R> __host__ __device__ constexpr int line_pad(int N) {
 }
 // Padded line length for TILE lines exchanged side by side (the line pass):
 // a warp holds 32/TILE positions of TILE lines, so the line-to-line offset
-// decides the banks.  Counting the shared-memory wavefronts of every exchange
-// of the Stockham stages gives the fewest with +1 except: FP32 TILE = 8, +2
-// (1024 instead of 1792 per N = 512 CTA); FP32 TILE = 4, +4 (1536 instead of
-// 3072 at N = 1024); FP64 TILE = 4, +2 (2048 instead of 2176 at N = 512).
+// decides the banks.  The extra words below give the fewest shared-memory
+// wavefronts over all exchanges of the Stockham stages, found by counting
+// them for every (N, E, TILE) the line-pass variants use; e.g. FP32
+// N = 512, TILE = 8: +2 gives 1024 wavefronts per CTA instead of 1792 with
+// +1, and N = 48, TILE = 32: +0 gives 576 instead of 2304.
+template <typename R> __host__ __device__ constexpr int line_pad_extra(int N, int TILE) {
+  if (sizeof(R) == 4) {
+    if (TILE >= 16) return (N == 16 || N == 48) ? 0 : 1;
+    if (TILE == 8) return N == 96 ? 0 : 2;
+    if (TILE == 4) return N == 192 ? 0 : 4;
+    if (TILE == 2) return N == 384 ? 0 : 8;
+    return 0;
+  }
+  if (TILE == 4) return 2;
+  if (TILE == 2) return N % 3 == 0 ? 4 : 0;
+  return TILE == 1 ? 0 : 1;
+}
 template <typename R> __host__ __device__ constexpr int line_pad_tile(int N, int TILE) {
-  return N + (N >> PadShift<R>::value) +
-         (sizeof(R) == 4 ? (TILE == 8 ? 2 : (TILE == 4 ? 4 : 1)) : (TILE == 4 ? 2 : 1));
+  return N + (N >> PadShift<R>::value) + line_pad_extra<R>(N, TILE);
 }
 
 // ----------------------------------------------------------------------------

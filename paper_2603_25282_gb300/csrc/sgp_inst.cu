@@ -1,7 +1,8 @@
 // sgp_inst.cu -- explicit instantiation of the pass kernels and their
-// launchers for one precision (SGP_REAL) and one kernel family (SGP_PART:
-// 0 = x-lines, 1 = strided lines).  Built several times with different
-// macros so that the instantiations compile in parallel.
+// launchers for one precision (SGP_REAL), one kernel family (SGP_PART:
+// 0 = x-lines, 1 = strided lines) and one kernel variant (SGP_VAR, see
+// sgp_launch.cuh).  Built once per combination so that the instantiations
+// compile in parallel; the observables kernels come with variant 0.
 #include "sgp_launch.cuh"
 
 #ifndef SGP_REAL
@@ -9,6 +10,15 @@
 #endif
 #ifndef SGP_PART
 #error "define SGP_PART (0 or 1)"
+#endif
+#ifndef SGP_VAR
+#define SGP_VAR 0
+#endif
+
+#if SGP_VAR == 3
+#define SGP_FOR_EACH_VN SGP_FOR_EACH_N_POW2
+#else
+#define SGP_FOR_EACH_VN SGP_FOR_EACH_N
 #endif
 
 namespace sgp {
@@ -28,18 +38,20 @@ cudaError_t prepare(K kern, size_t smem, int* done_dev) {
 }  // namespace
 
 typedef SGP_REAL Real;
+constexpr int V = SGP_VAR;
+constexpr int G = variant_geom<V>();
 
 #if SGP_PART == 0
 
 template <>
-PassGeom xpass_geom<Real>(int N) {
+PassGeom xpass_geom_v<Real, V>(int N) {
   switch (N) {
 #define SGP_CASE(NN)                                                        \
   case NN: {                                                                \
-    typedef XCfg<Real, NN, elems_per_thread<Real, NN>()> Cfg;               \
+    typedef XCfg<Real, NN, variant_elems<Real, NN, V>(), G> Cfg;            \
     return PassGeom{Cfg::THREADS, Cfg::ROWS, Cfg::SMEM};                    \
   }
-    SGP_FOR_EACH_N(SGP_CASE)
+    SGP_FOR_EACH_VN(SGP_CASE)
 #undef SGP_CASE
     default:
       return PassGeom{0, 0, 0};
@@ -48,33 +60,35 @@ PassGeom xpass_geom<Real>(int N) {
 
 template <int N>
 static cudaError_t xpass_prepare_n() {
-  constexpr int E = elems_per_thread<Real, N>();
+  constexpr int E = variant_elems<Real, N, V>();
   static int done = -1;
-  cudaError_t e = prepare(k_xpass<Real, N, E>, XCfg<Real, N, E>::SMEM, &done);
+  cudaError_t e = prepare(k_xpass<Real, N, E, G>, XCfg<Real, N, E, G>::SMEM, &done);
+#if SGP_VAR == 0
   if (e != cudaSuccess) return e;
   static int done_o = -1;
-  return prepare(k_obs_x<Real, N, E>, XCfg<Real, N, E>::SMEM, &done_o);
+  e = prepare(k_obs_x<Real, N, E>, XCfg<Real, N, E>::SMEM, &done_o);
+#endif
+  return e;
 }
 
 template <int N>
 static cudaError_t xpass_n(const XPassArgs<Real>& a, int members, cudaStream_t s) {
-  constexpr int E = elems_per_thread<Real, N>();
-  typedef XCfg<Real, N, E> Cfg;
+  constexpr int E = variant_elems<Real, N, V>();
+  typedef XCfg<Real, N, E, G> Cfg;
   cudaError_t e = xpass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.rows + Cfg::ROWS - 1) / Cfg::ROWS, members);
-  k_xpass<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  k_xpass<Real, N, E, G><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-
 template <>
-cudaError_t prepare_xpass<Real>(int N) {
+cudaError_t prepare_xpass_v<Real, V>(int N) {
   switch (N) {
 #define SGP_CASE(NN) \
   case NN:           \
     return xpass_prepare_n<NN>();
-    SGP_FOR_EACH_N(SGP_CASE)
+    SGP_FOR_EACH_VN(SGP_CASE)
 #undef SGP_CASE
     default:
       return cudaErrorInvalidValue;
@@ -82,18 +96,19 @@ cudaError_t prepare_xpass<Real>(int N) {
 }
 
 template <>
-cudaError_t launch_xpass<Real>(int N, const XPassArgs<Real>& a, int members, cudaStream_t s) {
+cudaError_t launch_xpass_v<Real, V>(int N, const XPassArgs<Real>& a, int members, cudaStream_t s) {
   switch (N) {
 #define SGP_CASE(NN) \
   case NN:           \
     return xpass_n<NN>(a, members, s);
-    SGP_FOR_EACH_N(SGP_CASE)
+    SGP_FOR_EACH_VN(SGP_CASE)
 #undef SGP_CASE
     default:
       return cudaErrorInvalidValue;
   }
 }
 
+#if SGP_VAR == 0
 template <int N>
 static cudaError_t obs_x_n(const ObsXArgs<Real>& a, int members, cudaStream_t s) {
   constexpr int E = elems_per_thread<Real, N>();
@@ -117,18 +132,19 @@ cudaError_t launch_obs_x<Real>(int N, const ObsXArgs<Real>& a, int members, cuda
       return cudaErrorInvalidValue;
   }
 }
+#endif
 
 #else  // SGP_PART == 1
 
 template <>
-PassGeom linepass_geom<Real>(int N) {
+PassGeom linepass_geom_v<Real, V>(int N) {
   switch (N) {
 #define SGP_CASE(NN)                                                        \
   case NN: {                                                                \
-    typedef LCfg<Real, NN, elems_per_thread<Real, NN>()> Cfg;               \
+    typedef LCfg<Real, NN, variant_elems<Real, NN, V>(), G> Cfg;            \
     return PassGeom{Cfg::THREADS, Cfg::TILE, Cfg::SMEM};                    \
   }
-    SGP_FOR_EACH_N(SGP_CASE)
+    SGP_FOR_EACH_VN(SGP_CASE)
 #undef SGP_CASE
     default:
       return PassGeom{0, 0, 0};
@@ -137,34 +153,36 @@ PassGeom linepass_geom<Real>(int N) {
 
 template <int N>
 static cudaError_t linepass_prepare_n() {
-  constexpr int E = elems_per_thread<Real, N>();
+  constexpr int E = variant_elems<Real, N, V>();
   static int done = -1;
-  cudaError_t e = prepare(k_linepass<Real, N, E>, LCfg<Real, N, E>::SMEM, &done);
+  cudaError_t e = prepare(k_linepass<Real, N, E, G>, LCfg<Real, N, E, G>::SMEM, &done);
+#if SGP_VAR == 0
   if (e != cudaSuccess) return e;
   static int done_o = -1;
-  return prepare(k_obs_line<Real, N, E>, LCfg<Real, N, E>::SMEM, &done_o);
+  e = prepare(k_obs_line<Real, N, E>, LCfg<Real, N, E>::SMEM, &done_o);
+#endif
+  return e;
 }
 
 template <int N>
 static cudaError_t linepass_n(const LPassArgs<Real>& a, int planes, int members,
                               cudaStream_t s) {
-  constexpr int E = elems_per_thread<Real, N>();
-  typedef LCfg<Real, N, E> Cfg;
+  constexpr int E = variant_elems<Real, N, V>();
+  typedef LCfg<Real, N, E, G> Cfg;
   cudaError_t e = linepass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
-  k_linepass<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  k_linepass<Real, N, E, G><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-
 template <>
-cudaError_t prepare_linepass<Real>(int N) {
+cudaError_t prepare_linepass_v<Real, V>(int N) {
   switch (N) {
 #define SGP_CASE(NN) \
   case NN:           \
     return linepass_prepare_n<NN>();
-    SGP_FOR_EACH_N(SGP_CASE)
+    SGP_FOR_EACH_VN(SGP_CASE)
 #undef SGP_CASE
     default:
       return cudaErrorInvalidValue;
@@ -172,19 +190,20 @@ cudaError_t prepare_linepass<Real>(int N) {
 }
 
 template <>
-cudaError_t launch_linepass<Real>(int N, const LPassArgs<Real>& a, int planes, int members,
-                                  cudaStream_t s) {
+cudaError_t launch_linepass_v<Real, V>(int N, const LPassArgs<Real>& a, int planes, int members,
+                                       cudaStream_t s) {
   switch (N) {
 #define SGP_CASE(NN) \
   case NN:           \
     return linepass_n<NN>(a, planes, members, s);
-    SGP_FOR_EACH_N(SGP_CASE)
+    SGP_FOR_EACH_VN(SGP_CASE)
 #undef SGP_CASE
     default:
       return cudaErrorInvalidValue;
   }
 }
 
+#if SGP_VAR == 0
 template <int N>
 static cudaError_t obs_line_n(const ObsLArgs<Real>& a, int planes, int members,
                               cudaStream_t s) {
@@ -210,6 +229,7 @@ cudaError_t launch_obs_line<Real>(int N, const ObsLArgs<Real>& a, int planes, in
       return cudaErrorInvalidValue;
   }
 }
+#endif
 
 #endif
 

@@ -328,10 +328,13 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
 // ----------------------------------------------------------------------------
 // x-pass kernel
 // ----------------------------------------------------------------------------
-template <typename R, int N, int E>
+// Geometry variant G: about 256 >> G threads per CTA (rows of the x-pass
+// side by side); G > 0 gives more, smaller CTAs for small grids.
+template <typename R, int N, int E, int G = 0>
 struct XCfg {
   static constexpr int T = N / E;
-  static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
+  static constexpr int CT = 256 >> G;
+  static constexpr int ROWS = (CT / T) > 0 ? (CT / T) : 1;
   static constexpr int THREADS = ROWS * T;
   static constexpr int LP = line_pad<R>(N);
   static constexpr int XCH = 2 * ROWS * LP;     // exchange buffers (complex)
@@ -346,11 +349,11 @@ struct XCfg {
 // staged in shared memory between the two transforms, as a plain loop over
 // points: one copy of its code (the unrolled form did not fit the
 // instruction cache) and registers only for the point being processed.
-template <typename R, int N, int E>
-__global__ void __launch_bounds__(XCfg<R, N, E>::THREADS, XCfg<R, N, E>::MINB)
+template <typename R, int N, int E, int G>
+__global__ void __launch_bounds__(XCfg<R, N, E, G>::THREADS, XCfg<R, N, E, G>::MINB)
 k_xpass(XPassArgs<R> a) {
   typedef cplx<R> C;
-  typedef XCfg<R, N, E> Cfg;
+  typedef XCfg<R, N, E, G> Cfg;
   constexpr int T = Cfg::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
@@ -429,12 +432,16 @@ k_xpass(XPassArgs<R> a) {
 // per tile at N = 512, i.e. 64 B contiguous per line element (a 256-thread,
 // 4-column variant measured slower: 32 B segments split HBM bursts between
 // CTAs).
-template <typename R, int N, int E>
+// Geometry variant G = 0: up to 512 threads per CTA, TILE clamped to
+// [TMIN, TMAX]; G > 0: about 512 >> G threads, TILE down to 1 column (more,
+// smaller CTAs for small grids, at the cost of shorter contiguous segments).
+template <typename R, int N, int E, int G = 0>
 struct LCfg {
   static constexpr int T = N / E;
   static constexpr int TMAX = sizeof(R) == 4 ? 32 : 16;
-  static constexpr int TMIN = sizeof(R) == 4 ? 4 : 2;
-  static constexpr int TILE = (512 / T) > TMAX ? TMAX : ((512 / T) < TMIN ? TMIN : (512 / T));
+  static constexpr int TMIN = G == 0 ? (sizeof(R) == 4 ? 4 : 2) : 1;
+  static constexpr int TT = 512 >> G;
+  static constexpr int TILE = (TT / T) > TMAX ? TMAX : ((TT / T) < TMIN ? TMIN : (TT / T));
   static constexpr int THREADS = TILE * T;
   static constexpr int LP = line_pad_tile<R>(N, TILE);
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * TILE * LP);
@@ -482,11 +489,11 @@ __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
   }
 }
 
-template <typename R, int N, int E>
-__global__ void __launch_bounds__(LCfg<R, N, E>::THREADS, LCfg<R, N, E>::MINB)
+template <typename R, int N, int E, int G>
+__global__ void __launch_bounds__(LCfg<R, N, E, G>::THREADS, LCfg<R, N, E, G>::MINB)
 k_linepass(LPassArgs<R> a) {
   typedef cplx<R> C;
-  typedef LCfg<R, N, E> Cfg;
+  typedef LCfg<R, N, E, G> Cfg;
   constexpr int T = Cfg::T;
   constexpr int TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem_raw[];

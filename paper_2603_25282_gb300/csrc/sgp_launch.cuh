@@ -1,5 +1,6 @@
 // sgp_launch.cuh -- host-side launchers for the pass kernels, dispatched on
-// the line length N (a compile-time parameter of every kernel).
+// the line length N (a compile-time parameter of every kernel) and on the
+// kernel variant V chosen by the autotuner.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -16,6 +17,7 @@ constexpr int elems_per_thread() {
 // Line lengths with compiled kernels.
 #define SGP_FOR_EACH_N(X) \
   X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+#define SGP_FOR_EACH_N_POW2(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 inline bool supported_n(int n) {
   switch (n) {
@@ -28,6 +30,37 @@ inline bool supported_n(int n) {
   }
 }
 
+// Kernel variants of a pass (the tile and radix schedules the autotuner
+// chooses from):
+//   0  default geometry (x-pass: about 256 threads per CTA; line pass: up
+//      to 512 threads, TILE >= 4 FP32 / 2 FP64 columns) and radix plan
+//   1  CTAs of about half the threads (line pass: TILE down to 1)
+//   2  CTAs of about a quarter of the threads
+//   3  FP32, N a power of two: radix-4 plan (4 elements per thread instead
+//      of 8: more stages, half the registers per line element)
+constexpr int kVariants = 4;
+
+template <typename R, int N, int V>
+constexpr int variant_elems() {
+  return V == 3 ? 4 : elems_per_thread<R, N>();
+}
+template <int V>
+constexpr int variant_geom() {
+  return V == 3 ? 0 : V;
+}
+
+// Does variant V exist for line length N (prec_bytes 4 or 8)?
+inline bool variant_exists(int prec_bytes, int N, int V) {
+  if (!supported_n(N) || V < 0 || V >= kVariants) return false;
+  if (V == 3) return prec_bytes == 4 && N % 3 != 0;
+  return true;
+}
+// Elements per thread of variant V (the twiddle table layout depends on it).
+inline int variant_elems_rt(int prec_bytes, int N, int V) {
+  if (V == 3) return 4;
+  return (N % 3 == 0) ? 6 : (prec_bytes == 4 ? 8 : 4);
+}
+
 // Launch geometry of one pass (for accounting and the observables scratch).
 struct PassGeom {
   int threads;
@@ -35,19 +68,70 @@ struct PassGeom {
   size_t smem;
 };
 
-template <typename R> PassGeom xpass_geom(int N);
-template <typename R> PassGeom linepass_geom(int N);
+// Per-variant entry points (explicitly instantiated in sgp_inst.cu).
+template <typename R, int V> PassGeom xpass_geom_v(int N);
+template <typename R, int V> PassGeom linepass_geom_v(int N);
+template <typename R, int V> cudaError_t prepare_xpass_v(int N);
+template <typename R, int V> cudaError_t prepare_linepass_v(int N);
+template <typename R, int V>
+cudaError_t launch_xpass_v(int N, const XPassArgs<R>& a, int members, cudaStream_t s);
+template <typename R, int V>
+cudaError_t launch_linepass_v(int N, const LPassArgs<R>& a, int planes, int members,
+                              cudaStream_t s);
 
+#define SGP_VARIANT_SWITCH(V, CALL, FAIL)                    \
+  switch (V) {                                               \
+    case 0: return CALL(0);                                  \
+    case 1: return CALL(1);                                  \
+    case 2: return CALL(2);                                  \
+    case 3:                                                  \
+      if constexpr (sizeof(R) == 4) return CALL(3);          \
+      return FAIL;                                           \
+    default: return FAIL;                                    \
+  }
+
+template <typename R>
+inline PassGeom xpass_geom(int N, int V = 0) {
+#define SGP_C(v) xpass_geom_v<R, v>(N)
+  SGP_VARIANT_SWITCH(V, SGP_C, (PassGeom{0, 0, 0}))
+#undef SGP_C
+}
+template <typename R>
+inline PassGeom linepass_geom(int N, int V = 0) {
+#define SGP_C(v) linepass_geom_v<R, v>(N)
+  SGP_VARIANT_SWITCH(V, SGP_C, (PassGeom{0, 0, 0}))
+#undef SGP_C
+}
 // Set the kernels' shared-memory attributes for line length N on the
 // current device (done before any stream capture).
-template <typename R> cudaError_t prepare_xpass(int N);
-template <typename R> cudaError_t prepare_linepass(int N);
+template <typename R>
+inline cudaError_t prepare_xpass(int N, int V = 0) {
+#define SGP_C(v) prepare_xpass_v<R, v>(N)
+  SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
+#undef SGP_C
+}
+template <typename R>
+inline cudaError_t prepare_linepass(int N, int V = 0) {
+#define SGP_C(v) prepare_linepass_v<R, v>(N)
+  SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
+#undef SGP_C
+}
+template <typename R>
+inline cudaError_t launch_xpass(int N, int V, const XPassArgs<R>& a, int members, cudaStream_t s) {
+#define SGP_C(v) launch_xpass_v<R, v>(N, a, members, s)
+  SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
+#undef SGP_C
+}
+template <typename R>
+inline cudaError_t launch_linepass(int N, int V, const LPassArgs<R>& a, int planes, int members,
+                                   cudaStream_t s) {
+#define SGP_C(v) launch_linepass_v<R, v>(N, a, planes, members, s)
+  SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
+#undef SGP_C
+}
+#undef SGP_VARIANT_SWITCH
 
-template <typename R>
-cudaError_t launch_xpass(int N, const XPassArgs<R>& a, int members, cudaStream_t s);
-template <typename R>
-cudaError_t launch_linepass(int N, const LPassArgs<R>& a, int planes, int members,
-                            cudaStream_t s);
+// Observables kernels (default geometry only).
 template <typename R>
 cudaError_t launch_obs_x(int N, const ObsXArgs<R>& a, int members, cudaStream_t s);
 template <typename R>

@@ -98,6 +98,11 @@ def lib():
         "sgp_destroy": (I, [P]),
         "sgp_observables_static": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                        I, I, ctypes.POINTER(Params), D, P, I, P, ctypes.POINTER(Obs)]),
+        "sgp_variant_exists": (I, [I, I, I]),
+        "sgp_set_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+        "sgp_get_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+        "sgp_autotune": (I, [P, I, I, ctypes.POINTER(ctypes.c_double)]),
+        "sgp_ensemble_autotune": (I, [P, I, I]),
         "sgp_record": (I, [P, LL, D, I, LL]),
         "sgp_backward": (I, [P, P, I, P, I, ctypes.POINTER(ctypes.c_double)]),
         "sgp_set_profiling": (I, [P, I]),
@@ -198,6 +203,40 @@ def get_time(ctx):
 def step(ctx, nsteps, dt, scheme="ts2"):
     s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
     _check(lib().sgp_step(ctx, int(nsteps), float(dt), s), ctx)
+
+
+SGP_TUNE_FORCE = 1
+N_VARIANTS = 4
+
+
+def variant_exists(prec, n, variant):
+    return bool(lib().sgp_variant_exists(PRECS[prec] if isinstance(prec, str) else prec,
+                                         int(n), int(variant)))
+
+
+def set_plan(ctx, variants):
+    """Kernel variant per axis (x-pass, y lines, z lines)."""
+    v = list(variants) + [0] * (3 - len(variants))
+    _check(lib().sgp_set_plan(ctx, (ctypes.c_int * 3)(*v)), ctx)
+
+
+def get_plan(ctx):
+    v = (ctypes.c_int * 3)()
+    _check(lib().sgp_get_plan(ctx, v), ctx)
+    return list(v)
+
+
+def autotune(ctx, reps=20, force=False, timings=False):
+    """sgp_autotune; returns the plan, and with timings=True also the
+    [axis][variant] ms per launch (None where absent)."""
+    ms = (ctypes.c_double * (3 * N_VARIANTS))() if timings else None
+    _check(lib().sgp_autotune(ctx, int(reps), SGP_TUNE_FORCE if force else 0, ms), ctx)
+    plan = get_plan(ctx)
+    if not timings:
+        return plan
+    tab = [[(ms[a * N_VARIANTS + v] if ms[a * N_VARIANTS + v] >= 0 else None)
+            for v in range(N_VARIANTS)] for a in range(3)]
+    return plan, tab
 
 
 def record(ctx, nsteps, dt, scheme="ts2", interval=0):
@@ -321,6 +360,15 @@ class Context:
     def substep(self, kind, delta):
         substep(self.handle, kind, delta)
 
+    def set_plan(self, variants):
+        set_plan(self.handle, variants)
+
+    def get_plan(self):
+        return get_plan(self.handle)
+
+    def autotune(self, reps=20, force=False, timings=False):
+        return autotune(self.handle, reps, force, timings)
+
     def record(self, nsteps, dt, scheme="ts2", interval=0):
         record(self.handle, nsteps, dt, scheme, interval)
 
@@ -424,6 +472,10 @@ class Ensemble:
     def step(self, nsteps, dt, scheme="ts2"):
         s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
         _echeck(lib().sgp_ensemble_step(self.handle, int(nsteps), float(dt), s), self.handle)
+
+    def autotune(self, reps=20, force=False):
+        _echeck(lib().sgp_ensemble_autotune(self.handle, int(reps), SGP_TUNE_FORCE if force else 0),
+                self.handle)
 
     def observables(self):
         arr = (Obs * self.count)()
