@@ -97,15 +97,18 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(wl, kernel):
+def measured_traffic(wl, kernel, plan):
     """DRAM bytes per launch from the committed ncu capture, or None when the
-    kernels have changed since it was taken (or none exists)."""
+    kernels or the kernel variants differ from the captured ones (or none
+    exists)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
     except Exception:
         return None
     if tr.get("csrc_sha256_16") != csrc_hash():
+        return None
+    if list(tr.get("plan", [])) != list(plan):
         return None
     return tr.get("bytes_per_launch", {}).get("%s:%s" % (wl, kernel))
 
@@ -293,7 +296,13 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- kernel variants chosen by the autotuner (untimed) -----------------
     ctx.set_state(dev_init, 0.0)
-    plan, tune_ms = ([0, 0, 0], None) if args.no_tune else ctx.autotune(reps=10, timings=True)
+    if args.plan:
+        ctx.set_plan([int(v) for v in args.plan.split(",")])
+        plan, tune_ms = ctx.get_plan(), None
+    elif args.no_tune:
+        plan, tune_ms = [0, 0, 0], None
+    else:
+        plan, tune_ms = ctx.autotune(reps=10, timings=True)
 
     # ---- device-resident timing -------------------------------------------
     ctx.set_state(dev_init, 0.0)
@@ -325,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kinds, key=lambda k: kinds[k][1])
     dom_avg_ms = kinds[dom][1] / kinds[dom][0]
     achieved = per_pass_bytes / (dom_avg_ms * 1e-3) / 1e9
-    traffic = measured_traffic(wl, dom)
+    traffic = measured_traffic(wl, dom, plan)
     bpp, bmin = bytes_per_point_step(dim, scheme, prec)
     step_gbs = bpp * pts * batch * args.steps / (ms * 1e-3) / 1e9
 
@@ -705,6 +714,7 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(GRAD_WORKLOADS) + sorted(ENS_WORKLOADS))
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default kernel variants, no autotuner")
+    ap.add_argument("--plan", default="", help="fixed kernel variants x,y[,z] instead of the autotuner")
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
