@@ -308,15 +308,20 @@ template <int DIR, typename C> struct Dft<6, DIR, C> {
 // ----------------------------------------------------------------------------
 // Stockham stages over NC components held in registers
 // ----------------------------------------------------------------------------
-// v[c][e]: element i + T*e of component c's line.  tw: W_N^k = exp(-2 pi i k/N),
-// k = 0..N-1 (TwE entries), in shared memory.  b0/b1: two padded exchange lines of this
-// thread group.  DIR = -1 forward, +1 inverse.  Every thread of the CTA must
-// call this (it contains __syncthreads).
-template <typename R, int N, int E, int DIR, int NC, int S, int NS>
+// v[c][e]: element i + T*e of component c's line.  tw: the stage twiddle
+// table (TwE entries), in shared memory.  Exchange buffers: buffer b of this
+// thread group's line is buf0 + b * bstride (padded, LP elements).  With
+// NB = 2 components alternate between two buffers and every component's
+// exchange has its own barrier; with NB = NC each component has its own
+// buffer, so a stage writes all components, passes one barrier and reads
+// them all (one more barrier before the next stage writes): the five
+// butterflies of a stage are independent work for the scheduler.  DIR = -1
+// forward, +1 inverse.  Every thread of the CTA must call this (barriers).
+template <typename R, int N, int E, int DIR, int NC, int NB, int S, int NS>
 struct FftStages {
   typedef cplx<R> C;
   __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const TwE<R>* tw,
-                                             C* b0, C* b1) {
+                                             C* buf0, int bstride) {
     constexpr int RD = radix_at(N, E, S);
     if constexpr (RD > 0) {
       constexpr int T = N / E;
@@ -335,9 +340,11 @@ struct FftStages {
           }
         }
       }
+      // NB = NC: the previous stage's reads of the buffers must be done
+      if constexpr (!LAST && NB != 2 && S > 0) __syncthreads();
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        C* buf = ((S * NC + c) & 1) ? b1 : b0;
+        C* buf = buf0 + (NB == 2 ? ((S * NC + c) & 1) : c) * bstride;
 #pragma unroll
         for (int k = 0; k < B; ++k) {
           C x[RD];
@@ -359,13 +366,22 @@ struct FftStages {
             for (int r = 0; r < RD; ++r) buf[padx<R>(idxD + r * NS)] = x[r];
           }
         }
-        if constexpr (!LAST) {
+        if constexpr (!LAST && NB == 2) {
           __syncthreads();
 #pragma unroll
           for (int e = 0; e < E; ++e) v[c][e] = buf[padx<R>(i + T * e)];
         }
       }
-      FftStages<R, N, E, DIR, NC, S + 1, NS * RD>::run(v, i, tw, b0, b1);
+      if constexpr (!LAST && NB != 2) {
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const C* buf = buf0 + c * bstride;
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[c][e] = buf[padx<R>(i + T * e)];
+        }
+      }
+      FftStages<R, N, E, DIR, NC, NB, S + 1, NS * RD>::run(v, i, tw, buf0, bstride);
     }
   }
 };
@@ -377,18 +393,20 @@ struct FftStages {
 // With the same rounded twiddle table, forward followed by this adjoint
 // equals N times the identity up to |W|^2 - 1 and butterfly rounding: the
 // twiddle phase errors cancel instead of accumulating over many steps.
-template <typename R, int N, int E, int NC, int S, int NS>
+template <typename R, int N, int E, int NC, int NB, int S, int NS>
 struct FftStagesAdj {
   typedef cplx<R> C;
   __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const TwE<R>* tw,
-                                             C* b0, C* b1) {
+                                             C* buf0, int bstride) {
     constexpr int RD = radix_at(N, E, S);
     if constexpr (RD > 0) {
       // later forward stages come first in the adjoint
-      FftStagesAdj<R, N, E, NC, S + 1, NS * RD>::run(v, i, tw, b0, b1);
+      FftStagesAdj<R, N, E, NC, NB, S + 1, NS * RD>::run(v, i, tw, buf0, bstride);
       constexpr int T = N / E;
       constexpr int B = E / RD;
       constexpr bool LAST = (NS * RD == N);
+      // the first buffer-using stage of the adjoint is the one before LAST
+      constexpr bool FIRSTBUF = (NS * RD * radix_at(N, E, S + 1) == N);
       constexpr int TOFF = tw_offset(N, E, S);
       TwE<R> w[B][RD];
 #pragma unroll
@@ -399,10 +417,20 @@ struct FftStagesAdj {
           for (int r = 1; r < RD; ++r) w[k][r] = tw_conj(tw[TOFF + (r - 1) * NS + j]);
         }
       }
+      if constexpr (!LAST && NB != 2) {
+        if constexpr (!FIRSTBUF) __syncthreads();     // earlier reads of the buffers done
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          C* buf = buf0 + c * bstride;
+#pragma unroll
+          for (int e = 0; e < E; ++e) buf[padx<R>(i + T * e)] = v[c][e];
+        }
+        __syncthreads();
+      }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        C* buf = ((S * NC + c) & 1) ? b1 : b0;
-        if constexpr (!LAST) {
+        C* buf = buf0 + (NB == 2 ? ((S * NC + c) & 1) : c) * bstride;
+        if constexpr (!LAST && NB == 2) {
 #pragma unroll
           for (int e = 0; e < E; ++e) buf[padx<R>(i + T * e)] = v[c][e];
           __syncthreads();
@@ -433,19 +461,19 @@ struct FftStagesAdj {
   }
 };
 
-// Forward (DIR = -1) or inverse (DIR = +1, the exact adjoint of the forward,
-// unnormalised) transform of NC lines held in layout A.
-template <typename R, int N, int E, int DIR, int NC>
-__device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i,
-                                          const TwE<R>* tw, cplx<R>* b0,
-                                          cplx<R>* b1) {
+// Line transforms of NC components (forward DIR = -1, inverse +1); NB
+// exchange buffers of bstride elements from buf0 (see FftStages).
+template <typename R, int N, int E, int DIR, int NC, int NB>
+__device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i, const TwE<R>* tw,
+                                          cplx<R>* buf0, int bstride) {
   static_assert(plan_ok(N, E), "no radix plan for this (N, E)");
+  static_assert(NB == 2 || NB == NC, "two alternating buffers or one per component");
   // the previous user of the exchange buffers may still be reading
   __syncthreads();
   if constexpr (DIR < 0)
-    FftStages<R, N, E, -1, NC, 0, 1>::run(v, i, tw, b0, b1);
+    FftStages<R, N, E, -1, NC, NB, 0, 1>::run(v, i, tw, buf0, bstride);
   else
-    FftStagesAdj<R, N, E, NC, 0, 1>::run(v, i, tw, b0, b1);
+    FftStagesAdj<R, N, E, NC, NB, 0, 1>::run(v, i, tw, buf0, bstride);
 }
 
 }  // namespace sgp

@@ -337,7 +337,9 @@ struct XCfg {
   static constexpr int ROWS = (CT / T) > 0 ? (CT / T) : 1;
   static constexpr int THREADS = ROWS * T;
   static constexpr int LP = line_pad<R>(N);
-  static constexpr int XCH = 2 * ROWS * LP;     // exchange buffers (complex)
+  static constexpr int NB = 5;                  // one exchange buffer per component (fits
+                                                // in the nonlinear staging area)
+  static constexpr int XCH = NB * ROWS * LP;    // exchange buffers (complex)
   static constexpr int STG = ROWS * 5 * N;      // nonlinear staging (complex)
   static constexpr int BUF = XCH > STG ? XCH : STG;
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)BUF;
@@ -380,8 +382,8 @@ k_xpass(XPassArgs<R> a) {
     for (int e = 0; e < E; ++e)
       v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
   C* b0 = xb + g * Cfg::LP;
-  C* b1 = xb + (Cfg::ROWS + g) * Cfg::LP;
-  if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  const int bstride = Cfg::ROWS * Cfg::LP;
+  if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if (a.mode & XP_NL) {
     C* stg = xb;                      // [ROWS][5][N], aliases the exchange buffers
     __syncthreads();                  // exchange buffers free, s_rot visible
@@ -416,7 +418,7 @@ k_xpass(XPassArgs<R> a) {
 #pragma unroll
       for (int e = 0; e < E; ++e) v[c][e] = stg[(g * 5 + c) * N + i + T * e];
   }
-  if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+  if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if (valid) {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
@@ -444,7 +446,10 @@ struct LCfg {
   static constexpr int TILE = (TT / T) > TMAX ? TMAX : ((TT / T) < TMIN ? TMIN : (TT / T));
   static constexpr int THREADS = TILE * T;
   static constexpr int LP = line_pad_tile<R>(N, TILE);
-  static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(2 * TILE * LP);
+  // two alternating exchange buffers (one per component measured 3% slower
+  // here: the larger buffers cost more than the barriers they save)
+  static constexpr int NB = 2;
+  static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(NB * TILE * LP);
   static constexpr int MINB = (THREADS <= 256 && 2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
@@ -514,8 +519,8 @@ k_linepass(LPassArgs<R> a) {
     for (int e = 0; e < E; ++e)
       v[c][e] = valid ? base[(size_t)c * a.ntot + e * step] : mkc((R)0, (R)0);
   C* b0 = xb + col * Cfg::LP;
-  C* b1 = xb + (TILE + col) * Cfg::LP;
-  if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+  const int bstride = TILE * Cfg::LP;
+  if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if (a.mode & LP_MIX) {
     const int pm = valid ? xcol : 0;   // idle threads of a ragged tile read mode 0
 #pragma unroll
@@ -530,7 +535,7 @@ k_linepass(LPassArgs<R> a) {
       for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
     }
   }
-  if (a.mode & LP_INV) fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  if (a.mode & LP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if (valid) {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
@@ -633,8 +638,8 @@ k_obs_x(ObsXArgs<R> a) {
     for (int e = 0; e < E; ++e)
       v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
   C* b0 = xb + g * Cfg::LP;
-  C* b1 = xb + (Cfg::ROWS + g) * Cfg::LP;
-  fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+  const int bstride = Cfg::ROWS * Cfg::LP;
+  fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = i + T * e;
@@ -643,7 +648,7 @@ k_obs_x(ObsXArgs<R> a) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c][e] = cscale(cmuli(v[c][e]), f);
   }
-  fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   double acc[13];
 #pragma unroll
   for (int k = 0; k < 13; ++k) acc[k] = 0.0;
@@ -734,8 +739,8 @@ k_obs_line(ObsLArgs<R> a) {
     for (int e = 0; e < E; ++e)
       v[c][e] = valid ? base[(size_t)c * a.ntot + e * step] : mkc((R)0, (R)0);
   C* b0 = xb + col * Cfg::LP;
-  C* b1 = xb + (TILE + col) * Cfg::LP;
-  fft_lines<R, N, E, -1, 5>(v, i, tw, b0, b1);
+  const int bstride = TILE * Cfg::LP;
+  fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = i + T * e;
@@ -744,7 +749,7 @@ k_obs_line(ObsLArgs<R> a) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c][e] = cscale(cmuli(v[c][e]), f);
   }
-  fft_lines<R, N, E, +1, 5>(v, i, tw, b0, b1);
+  fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   double acc[3] = {0.0, 0.0, 0.0};
   if (valid) {
     const double x = a.x0 + xcol * a.hx;
