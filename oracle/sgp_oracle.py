@@ -454,3 +454,94 @@ def component_errors(a, ref):
         out.append(float(np.linalg.norm((a[l] - ref[l]).ravel())
                          / np.linalg.norm(ref[l].ravel())))
     return out
+
+
+# --------------------------------------------------------------------------
+# Lab-frame output by rotation-shear decomposition (Sec. 3.1, Eqs. (RSDA1),
+# (RSDA2)); test infrastructure like the rest of this module
+# --------------------------------------------------------------------------
+def shear(f, grid, axis, coef_times_other):
+    """exp(c(x) d_axis) f: translate every line along `axis` (0 = x, 1 = y)
+    by c, where c varies with the other coordinate: c = coef_times_other,
+    an array broadcast to the grid.  In Fourier space along the line the
+    mode nu_p is multiplied by exp(i nu_p c) (a translation by c)."""
+    nu = grid.wavenumbers()[axis]
+    ax = -1 - axis                     # array axis of the line
+    fh = np.fft.fft(f, axis=ax)
+    fh = fh * np.exp(1j * nu * coef_times_other)
+    return np.fft.ifft(fh, axis=ax)
+
+
+def rotate_quarter(f, k):
+    """g(x) = f(R_{k pi/2} x) exactly on a square periodic grid, R_a the
+    counter-clockwise rotation by a; x_j = -L + j h, so -x_j = x_{(N-j) mod N}."""
+    k %= 4
+    out = f
+    for _ in range(k):
+        # g(x, y) = f(-y, x):  G[iy, ix] = A[ix, (N - iy) mod N]
+        n = out.shape[-1]
+        idx = (-np.arange(n)) % n
+        out = np.swapaxes(out, -1, -2)[..., idx, :]
+    return out
+
+
+def rotate_rsda(f, grid, theta):
+    """g(x) = f(R_theta x) (R_theta counter-clockwise) by exact quarter turns
+    and the three shears of Eq. (RSDA2) for the remaining angle in
+    [-pi/4, pi/4]: exp(a y d_x) exp(b x d_y) exp(a y d_x) with
+    a = -tan(theta_r / 2), b = sin(theta_r).  Quarter turns need a square
+    grid (equal N and L in x and y)."""
+    k = int(np.round(theta / (0.5 * math.pi)))
+    thr = theta - k * 0.5 * math.pi
+    if k % 4:
+        if grid.n[0] != grid.n[1] or grid.L[0] != grid.L[1]:
+            raise ValueError("quarter turns need a square grid")
+        f = rotate_quarter(f, k)
+    X = grid.coords()
+    a = -math.tan(0.5 * thr)
+    b = math.sin(thr)
+    g = shear(f, grid, 0, a * X[1])
+    g = shear(g, grid, 1, b * X[0])
+    return shear(g, grid, 0, a * X[1])
+
+
+def lab_frame_field(Phi, grid, omega, t):
+    """psi_l(x, t) = exp(i l Omega t) phi_l(R(t)^T x, t), the inverse of the
+    mapping (mapping), evaluated on the grid as in Eq. (RSDA2)."""
+    th = omega * t
+    g = rotate_rsda(Phi, grid, th)
+    return np.exp(1j * MS * th).reshape((5,) + (1,) * grid.dim) * g
+
+
+def rotating_frame_field(Psi, grid, omega, t):
+    """phi_l(x, t) = exp(-i l Omega t) psi_l(R(t) x, t), Eq. (RSDA1)."""
+    th = omega * t
+    g = rotate_rsda(Psi, grid, -th)
+    return np.exp(-1j * MS * th).reshape((5,) + (1,) * grid.dim) * g
+
+
+def lab_trap(grid, prm):
+    """V(x) of Eq. (harmonic) in the lab frame."""
+    X = grid.coords()
+    V = prm.gx ** 2 * X[0] ** 2 + prm.gy ** 2 * X[1] ** 2
+    if grid.dim == 3:
+        V = V + prm.gz ** 2 * X[2] ** 2
+    return 0.5 * V
+
+
+def lab_nonlinear_substep(Psi, grid, prm, delta):
+    """Eq. (solution2) in the lab frame (trap V(x)): the rotating-frame flow
+    with the rotation angle set to zero."""
+    p0 = Params(**{**prm.__dict__, "omega": 0.0})
+    return nonlinear_substep(Psi, grid, p0, delta, 0.0)
+
+
+def algorithm1_lab_step(Psi, grid, prm, t, tau, props=None):
+    """One step of Algorithm 1 as printed, in the lab frame: N(tau/2) with
+    V(x), the mapping (RSDA1) at t, the linear flow (sl1) over tau, the
+    inverse mapping (RSDA2) at t + tau, N(tau/2)."""
+    Psi = lab_nonlinear_substep(Psi, grid, prm, 0.5 * tau)
+    Phi = rotating_frame_field(Psi, grid, prm.omega, t)
+    Phi = linear_substep(Phi, grid, prm, tau, props)
+    Psi = lab_frame_field(Phi, grid, prm.omega, t + tau)
+    return lab_nonlinear_substep(Psi, grid, prm, 0.5 * tau)
