@@ -143,6 +143,22 @@ sgp_status sgp_set_state(sgp_ctx* ctx, const void* src, int src_on_device,
  * returning; with a device pointer it is asynchronous. */
 sgp_status sgp_get_state(sgp_ctx* ctx, void* dst, int dst_on_device);
 
+/* Lab-frame field at the current time t (Sec. 3.1): psi_l(x, t) =
+ * exp(i l Omega t) phi_l(R(t)^T x, t), the inverse of the mapping
+ * (mapping), evaluated on the grid as in Eq. (RSDA2).  The rotation by
+ * Omega t (each member its own Omega) is done as exact quarter turns, which
+ * need a square x-y grid (equal N and L) and are only used when
+ * |Omega t| mod pi/2 leaves a remainder beyond pi/4, and three shears
+ * exp(a y d_x) exp(b x d_y) exp(a y d_x), a = -tan(r/2), b = sin(r), for the
+ * remainder r (each a line FFT, a phase per mode with its angle in FP64,
+ * the inverse FFT).  In 3D the rotation is about z.  Accurate to the
+ * spectral accuracy of the grid for fields that decay inside the domain
+ * (the shears are periodic translations).  dst: the state layout of
+ * sgp_get_state, on the device if dst_on_device, else host memory.  The
+ * context's state is not changed.  Synchronises.  Errors: SGP_EINVAL for
+ * NULL dst, dim 1, or a non-square grid when quarter turns are needed. */
+sgp_status sgp_get_state_lab(sgp_ctx* ctx, void* dst, int dst_on_device);
+
 /* Current time t (host copy, FP64). */
 sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
 

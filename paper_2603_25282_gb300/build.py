@@ -26,6 +26,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.
 UNITS = [
     ("api", "sgp_api.cu", []),
     ("adjoint", "sgp_adjoint.cu", []),
+    ("lab", "sgp_lab.cu", []),
 ] + [
     ("inst_%s_%s_v%d" % (r[0:3], "xl"[part], v), "sgp_inst.cu",
      ["-DSGP_REAL=%s" % r, "-DSGP_PART=%d" % part, "-DSGP_VAR=%d" % v])

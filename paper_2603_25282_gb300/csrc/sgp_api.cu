@@ -14,6 +14,7 @@
 
 #include "../../include/sgp.h"
 #include "sgp_adjoint.cuh"
+#include "sgp_lab.cuh"
 #include "sgp_launch.cuh"
 
 using namespace sgp;
@@ -221,6 +222,8 @@ struct AdjRec {
   size_t spec_cap = 0;
   double* dp = nullptr;            // [batch][GP_N]
   size_t dp_cap = 0;
+  void* lab = nullptr;             // one member's field, lab-frame output
+  size_t lab_cap = 0;
   double* part = nullptr;          // per-block partial sums [batch][blocks][GP_N]
   size_t part_cap = 0;
   // captured full-length segment and what it was captured for
@@ -671,6 +674,7 @@ void free_adj(sgp_ctx* c) {
   cudaFree(r.spec);
   cudaFree(r.dp);
   cudaFree(r.part);
+  cudaFree(r.lab);
   r = AdjRec();
 }
 
@@ -922,6 +926,66 @@ sgp_status backward_sweep(sgp_ctx* c) {
   }
   c->launches++;
   SGP_CUDA(c, launch_reduce_params(r.part, nblocks, c->batch, r.dp, c->stream));
+  return SGP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// lab-frame output (Eq. (RSDA2)): quarter turns + three shears + exp(i l Omega t)
+// ----------------------------------------------------------------------------
+template <typename R>
+sgp_status state_lab(sgp_ctx* c, void* dst, int on_device) {
+  AdjRec& r = c->adj;
+  const size_t sbm = (size_t)5 * c->ntot * c->elem;
+  SGP_TRY(ensure_buf(c, &r.lab, &r.lab_cap, sbm));
+  const double q = 0.5 * kPi;
+  for (int m = 0; m < c->batch; ++m) {
+    const double th = c->prm[m].omega * c->t;
+    const long long k = (long long)std::llround(th / q);
+    const double thr = th - (double)k * q;
+    const int kk = (int)(((k % 4) + 4) % 4);
+    if (kk && (c->n[0] != c->n[1] || c->L[0] != c->L[1]))
+      return fail(c, SGP_EINVAL,
+                  "rotation by %.3f rad needs quarter turns: the x-y grid must be square", th);
+    const char* src = (const char*)c->field + sbm * m;
+    cplx<R>* A = (cplx<R>*)r.lab;
+    if (kk) {
+      c->launches++;
+      SGP_CUDA(c, launch_quarter<R>((const cplx<R>*)src, A, c->n[0], c->ntot, kk, c->stream));
+    } else {
+      SGP_CUDA(c, cudaMemcpyAsync(A, src, sbm, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    ShearArgs<R> rows{};
+    rows.field = A;
+    rows.tw = (const TwE<R>*)c->tw[0];
+    rows.ntot = c->ntot;
+    rows.rows = c->n[1] * c->n[2];
+    rows.ny = c->n[1];
+    rows.coef = -std::tan(0.5 * thr);
+    rows.o0 = -c->L[1];
+    rows.h0 = c->h[1];
+    rows.kfac = kPi / c->L[0];
+    ShearArgs<R> cols{};
+    cols.field = A;
+    cols.tw = (const TwE<R>*)c->tw[1];
+    cols.ntot = c->ntot;
+    cols.rows = c->n[0];
+    cols.line_stride = c->n[0];
+    cols.plane_stride = (long long)c->n[0] * c->n[1];
+    cols.coef = std::sin(thr);
+    cols.o0 = -c->L[0];
+    cols.h0 = c->h[0];
+    cols.kfac = kPi / c->L[1];
+    c->launches += 3;
+    SGP_CUDA(c, launch_shear_rows<R>(c->n[0], rows, c->stream));
+    SGP_CUDA(c, launch_shear_cols<R>(c->n[1], cols, c->n[2], c->stream));
+    rows.lab_phase = 1;
+    rows.theta = th;
+    SGP_CUDA(c, launch_shear_rows<R>(c->n[0], rows, c->stream));
+    SGP_CUDA(c, cudaMemcpyAsync((char*)dst + sbm * m, A, sbm,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+  }
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
   return SGP_OK;
 }
 
@@ -1337,6 +1401,15 @@ sgp_status sgp_get_state(sgp_ctx* c, void* dst, int dst_on_device) {
                               c->stream));
   if (!dst_on_device) SGP_CUDA(c, cudaStreamSynchronize(c->stream));
   return SGP_OK;
+}
+
+sgp_status sgp_get_state_lab(sgp_ctx* c, void* dst, int dst_on_device) {
+  if (!c) return SGP_EINVAL;
+  if (!dst) return fail(c, SGP_EINVAL, "NULL dst");
+  if (c->dim < 2) return fail(c, SGP_EINVAL, "lab frame needs dim 2 or 3");
+  DeviceGuard guard(c->device);
+  return c->prec == SGP_F32 ? state_lab<float>(c, dst, dst_on_device)
+                            : state_lab<double>(c, dst, dst_on_device);
 }
 
 sgp_status sgp_get_time(const sgp_ctx* c, double* t) {

@@ -90,6 +90,7 @@ def lib():
         "sgp_set_state": (I, [P, P, I, D]),
         "sgp_get_state": (I, [P, P, I]),
         "sgp_get_time": (I, [P, ctypes.POINTER(ctypes.c_double)]),
+        "sgp_get_state_lab": (I, [P, P, I]),
         "sgp_step": (I, [P, LL, D, I]),
         "sgp_substep": (I, [P, I, D]),
         "sgp_observables": (I, [P, ctypes.POINTER(Obs)]),
@@ -191,6 +192,12 @@ def set_state(ctx, src, dtype, t0=0.0):
 def get_state(ctx, dst, dtype):
     ptr, dev, _keep = _ptr(dst, dtype)
     _check(lib().sgp_get_state(ctx, ctypes.c_void_p(ptr), dev), ctx)
+    return dst
+
+
+def get_state_lab(ctx, dst, dtype):
+    ptr, dev, _keep = _ptr(dst, dtype)
+    _check(lib().sgp_get_state_lab(ctx, ctypes.c_void_p(ptr), dev), ctx)
     return dst
 
 
@@ -348,6 +355,13 @@ class Context:
         if out is None:
             out = np.empty(self.shape, dtype=self.dtype)
         get_state(self.handle, out, self.dtype)
+        return out
+
+    def get_state_lab(self, out=None):
+        """Lab-frame field at the current time (sgp_get_state_lab)."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        get_state_lab(self.handle, out, self.dtype)
         return out
 
     @property
