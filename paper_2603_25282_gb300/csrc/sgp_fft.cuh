@@ -217,6 +217,30 @@ __device__ __forceinline__ float2 tw_mul(float2 x, TwE<float> w) {
 __device__ __forceinline__ double2 tw_mul(double2 x, TwE<double> w) {
   return make_double2(fma(x.x, w.hi.x, -x.y * w.hi.y), fma(x.x, w.hi.y, x.y * w.hi.x));
 }
+// The same product with each of the four partial products rounded once with
+// its own correction, then combined.  Needed when a twiddle component is
+// exact in FP32 (+-1/2, as at multiples of 30 degrees in the plans with a
+// factor 3): in tw_mul the lo term of the other component is then added to
+// an exactly representable partial product, stays below half an ulp and is
+// rounded away every time, and since the hi part of sqrt(3)/2 is rounded
+// down the product is always slightly too small (a steady mass loss of a few
+// 1e-9 per transform).  Here no correction meets an exact value alone.
+__device__ __forceinline__ float2 tw_mul_split(float2 x, TwE<float> w) {
+  const float p = fmaf(x.x, w.hi.x, x.x * w.lo.x);
+  const float q = fmaf(x.y, w.hi.y, x.y * w.lo.y);
+  const float r = fmaf(x.x, w.hi.y, x.x * w.lo.y);
+  const float s = fmaf(x.y, w.hi.x, x.y * w.lo.x);
+  return make_float2(p - q, r + s);
+}
+__device__ __forceinline__ double2 tw_mul_split(double2 x, TwE<double> w) { return tw_mul(x, w); }
+// twiddle product of a length-N plan
+template <int N, typename C, typename W>
+__device__ __forceinline__ C tw_apply(C x, W w) {
+  if constexpr (N % 3 == 0)
+    return tw_mul_split(x, w);
+  else
+    return tw_mul(x, w);
+}
 
 template <int RD, int DIR, typename C> struct Dft;
 
@@ -352,7 +376,7 @@ struct FftStages {
           for (int r = 0; r < RD; ++r) {
             x[r] = v[c][k + r * B];
             if constexpr (NS > 1) {
-              if (r > 0) x[r] = tw_mul(x[r], w[k][r]);
+              if (r > 0) x[r] = tw_apply<N>(x[r], w[k][r]);
             }
           }
           Dft<RD, DIR, C>::run(x);
@@ -451,7 +475,7 @@ struct FftStagesAdj {
 #pragma unroll
           for (int r = 0; r < RD; ++r) {
             if constexpr (NS > 1) {
-              if (r > 0) x[r] = tw_mul(x[r], w[k][r]);
+              if (r > 0) x[r] = tw_apply<N>(x[r], w[k][r]);
             }
             v[c][k + r * B] = x[r];
           }

@@ -1,11 +1,8 @@
 """Dynamical laws of Sec. 2 on the GPU path, Example 3 set-up: c = (120, 1, 1),
 Omega = 0.2, the Example 3 initial data, [-24, 24]^2, TS4 with tau = 1e-3 up
-to t = 12, FP32 fields (FP64 sums), observables every 10 steps.  The grid is
-N = 1024 (h = 3/64, finer than the example's h = 1/16, N = 768): FP32 line
-transforms of length 3*2^k lose about 5e-9 of the mass per substep here,
-which over 12 000 TS4 steps would exceed the conservation tolerances below,
-while power-of-two lengths conserve it to ~1e-10 per substep.  Three cases,
-as in the paper's example:
+to t = 12, FP32 fields (FP64 sums), observables every 10 steps, on the
+example's grid h = 1/16 (N = 768 = 3 * 256).  Three cases, as in the paper's
+example:
 
   (i)   gamma = 0, isotropic trap: mass, magnetization and <L_z> conserved;
         delta_r(t) follows Eq. (delta_r) (real radially symmetric data, so
@@ -31,7 +28,7 @@ from tests import lab_rk4
 
 pytestmark = pytest.mark.gpu
 
-N, L, TAU, T_END, EVERY = 1024, 24.0, 1e-3, 12.0, 10
+N, L, TAU, T_END, EVERY = 768, 24.0, 1e-3, 12.0, 10
 S6H = math.sqrt(6.0) / 2.0
 
 

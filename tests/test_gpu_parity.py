@@ -306,3 +306,20 @@ def test_ensemble_of_different_grids_f64():
             assert O.rel_l2(ens.get_member_state(k), ref) < 1e-10
             r = O.observables(ref, O.Grid(n, L), O.Params(**plist[k]), t)
             assert abs(obs[k]["mass"] - r["mass"]) < 1e-12
+
+
+@pytest.mark.parametrize("n,L", [((96, 96), 6.0), ((192, 192), 6.0)])
+def test_fp32_mass_drift_on_radix3_lengths(n, L):
+    """FP32 mass over 1000 TS4 steps on grids of length 3*2^k (plans with a
+    radix-6 stage and twiddles at multiples of 30 degrees), trap on: the
+    drift stays at the power-of-two level (it was ~1e-5 when the twiddle
+    product lost its correction against exact +-1/2 components)."""
+    prm = _params(c0=0.0, c1=0.0, c2=0.0, gamma=0.0, omega=0.2)
+    c = _ctx(n, L, "f32", **prm)
+    psi = inputs.ini_example3(n, L)
+    c.set_state(psi[None].astype(np.complex64).copy(), 0.0)
+    m0 = c.observables()[0]["mass"]
+    c.step(1000, 1e-3, "ts4")
+    m1 = c.observables()[0]["mass"]
+    c.close()
+    assert abs(m1 / m0 - 1) < 5e-6
