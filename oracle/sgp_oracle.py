@@ -347,12 +347,21 @@ def substep_sequence(scheme):
     TS2: N(tau/2) L(tau) N(tau/2) -- Algorithm 1.
     TS4: N(a1) L(b1) N(a2) L(b2) N(a2) L(b1) N(a1) -- the fourth-order
     coefficients of Sec. 3.3 with the nonlinear flow taking the a_j.
+    The same compositions with the roles of the two flows exchanged (the
+    other reading of Sec. 3.3's coefficient list, equally valid):
+    TS2_LNL: L(tau/2) N(tau) L(tau/2);
+    TS4_L:   L(a1) N(b1) L(a2) N(b2) L(a2) N(b1) L(a1).
     """
     if scheme == "ts2":
         return [("N", 0.5), ("L", 1.0), ("N", 0.5)]
     if scheme == "ts4":
         return [("N", TS4_A1), ("L", TS4_B1), ("N", TS4_A2), ("L", TS4_B2),
                 ("N", TS4_A2), ("L", TS4_B1), ("N", TS4_A1)]
+    if scheme == "ts2_lnl":
+        return [("L", 0.5), ("N", 1.0), ("L", 0.5)]
+    if scheme == "ts4_l":
+        return [("L", TS4_A1), ("N", TS4_B1), ("L", TS4_A2), ("N", TS4_B2),
+                ("L", TS4_A2), ("N", TS4_B1), ("L", TS4_A1)]
     raise ValueError(scheme)
 
 

@@ -313,6 +313,25 @@ def test_temporal_orders_two_and_four():
     assert 3.8 < r4 < 4.2, r4
 
 
+@pytest.mark.parametrize("sch,order", [("ts2_lnl", 2), ("ts4_l", 4)])
+def test_linear_outer_compositions_orders(sch, order):
+    """The compositions with the flows' roles exchanged reach the same
+    solution (a TS4 reference) at their own orders, and differ from the
+    default compositions at finite tau (they are different schemes)."""
+    n, L = (48, 48), 8.0
+    g = O.Grid(n, L)
+    p = O.Params(omega=0.3, gamma=0.4, c0=30, c1=-1, c2=1)
+    phi = inputs.gaussian_random_phase(n, L, seed=1, amp=0.2)
+    pr = O.Propagator(g, p)
+    T = 0.2
+    ref, _ = pr.run(phi, 0.0, T / 160, 160, "ts4")
+    e = [O.rel_l2(pr.run(phi, 0.0, T / k, k, sch)[0], ref) for k in (10, 20)]
+    r = math.log2(e[0] / e[1])
+    assert abs(r - order) < 0.15, r
+    other = "ts2" if order == 2 else "ts4"
+    assert O.rel_l2(pr.run(phi, 0.0, T / 10, 10, sch)[0], pr.run(phi, 0.0, T / 10, 10, other)[0]) > 1e-9
+
+
 def _golden_table1():
     path = os.path.join(os.path.dirname(__file__), "golden", "table1_2d_temporal.txt")
     rows = {}
