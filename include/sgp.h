@@ -63,8 +63,12 @@ typedef enum { SGP_F32 = 32, SGP_F64 = 64 } sgp_prec;
 /* Compositions of Sec. 3.3.  TS2: N(tau/2) L(tau) N(tau/2) (Algorithm 1).
  * TS4: N(a1 tau) L(b1 tau) N(a2 tau) L(b2 tau) N(a2 tau) L(b1 tau) N(a1 tau)
  * with the fourth-order coefficients of Sec. 3.3, the nonlinear flow taking
- * the a_j and the linear flow the b_j.  Time advances in the L substeps. */
-typedef enum { SGP_TS2 = 0, SGP_TS4 = 1 } sgp_scheme;
+ * the a_j and the linear flow the b_j.  The same compositions with the two
+ * flows' roles exchanged (the other reading of the coefficient list, equally
+ * valid, with a different error constant): TS2_LNL: L(tau/2) N(tau) L(tau/2);
+ * TS4_LOUTER: L(a1 tau) N(b1 tau) L(a2 tau) N(b2 tau) L(a2 tau) N(b1 tau)
+ * L(a1 tau).  Time advances in the L substeps. */
+typedef enum { SGP_TS2 = 0, SGP_TS4 = 1, SGP_TS2_LNL = 2, SGP_TS4_LOUTER = 3 } sgp_scheme;
 
 /* Flags of sgp_autotune. */
 enum { SGP_TUNE_FORCE = 1 };
@@ -163,10 +167,13 @@ sgp_status sgp_get_state_lab(sgp_ctx* ctx, void* dst, int dst_on_device);
 sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
 
 /* Advance every batch member by nsteps steps of size dt with the given
- * composition (Sec. 3.3; TS2 is Algorithm 1).  Adjacent nonlinear substeps of
- * consecutive steps, taken at the same time, are merged into one exact
- * nonlinear flow (the flow property of Eq. (solution2)), so a call costs
- * nsteps linear and nsteps+1 nonlinear substeps for TS2.  Runs of 128 steps
+ * composition (Sec. 3.3; TS2 is Algorithm 1, sgp_scheme lists all four).
+ * Substeps of the same kind where consecutive steps meet are merged: the
+ * nonlinear ones at the same time into one exact nonlinear flow (the flow
+ * property of Eq. (solution2)), the linear ones (time-independent in the
+ * rotating frame) into one linear flow, so a call costs nsteps linear and
+ * nsteps+1 nonlinear substeps for TS2 (the reverse for TS2_LNL, which also
+ * opens and closes the run with an x-transform pass).  Runs of 128 steps
  * or more are issued as replays of a captured CUDA graph of 64 steps (one
  * extra nonlinear pass per 64 steps, where the chunks meet); the time is
  * kept on the device in FP64 and advanced inside the graph.  The field is

@@ -523,37 +523,76 @@ sgp_status linear_middle(sgp_ctx* c, double delta) {
 
 // substep pattern of one step, Sec. 3.3
 std::vector<std::pair<char, double>> scheme_seq(int scheme) {
-  if (scheme == SGP_TS2) return {{'N', 0.5}, {'L', 1.0}, {'N', 0.5}};
-  return {{'N', kA1}, {'L', kB1}, {'N', kA2}, {'L', kB2}, {'N', kA2}, {'L', kB1}, {'N', kA1}};
+  switch (scheme) {
+    case SGP_TS2: return {{'N', 0.5}, {'L', 1.0}, {'N', 0.5}};
+    case SGP_TS2_LNL: return {{'L', 0.5}, {'N', 1.0}, {'L', 0.5}};
+    case SGP_TS4_LOUTER:
+      return {{'L', kA1}, {'N', kB1}, {'L', kA2}, {'N', kB2}, {'L', kA2}, {'N', kB1}, {'L', kA1}};
+    default:
+      return {{'N', kA1}, {'L', kB1}, {'N', kA2}, {'L', kB2}, {'N', kA2}, {'L', kB1}, {'N', kA1}};
+  }
+}
+
+bool valid_scheme(int scheme) {
+  return scheme == SGP_TS2 || scheme == SGP_TS4 || scheme == SGP_TS2_LNL || scheme == SGP_TS4_LOUTER;
+}
+
+struct SubRec {
+  char kind;
+  double delta;
+  double toff;     // time of the substep relative to the start of the run
+};
+
+// Substeps of n steps of the scheme, with the substeps of the same kind that
+// meet at a step boundary merged: nonlinear flows at the same time (the flow
+// of Eq. (solution2) over a then b is the flow over a + b) and linear flows
+// (time-independent in the rotating frame, so L(a) L(b) = L(a + b)).  Time
+// advances in the linear substeps; the substep at the end of step s is at
+// (s + 1) dt.
+std::vector<SubRec> merged_substeps(int scheme, long long n, double dt) {
+  const auto seq = scheme_seq(scheme);
+  std::vector<SubRec> subs;
+  for (long long s = 0; s < n; ++s) {
+    double sub = 0.0;
+    for (size_t k = 0; k < seq.size(); ++k) {
+      const double delta = seq[k].second * dt;
+      const char kind = seq[k].first;
+      const double toff = (k == seq.size() - 1) ? (double)(s + 1) * dt : (double)s * dt + sub * dt;
+      if (kind == 'L') sub += seq[k].second;
+      if (k == 0 && !subs.empty() && subs.back().kind == kind)
+        subs.back().delta += delta;        // meets the previous step's last substep
+      else
+        subs.push_back({kind, delta, toff});
+    }
+  }
+  return subs;
 }
 
 // Issue nsteps of the composition from the device time *t_dev and advance
-// it by nsteps*dt.  Adjacent nonlinear substeps at the same time are merged
-// (exact flow property), so the pass sequence is N L N L ... L N with the N
-// as x-passes and the L as line passes.  Physical space in and out.
+// it by nsteps*dt, physical space in and out.  The merged substeps become
+// passes: a nonlinear flow is an x-pass (inverse x-FFT if the field is
+// x-spectral, the flow, forward x-FFT if a linear flow follows); a linear
+// flow is the line passes on the x-spectral field (a forward x-pass first if
+// the field is physical).  With the nonlinear flow outside (TS2, TS4) a step
+// is N L N L ... with one x-pass per N; with the linear flow outside the
+// run starts with a forward x-pass and ends with an inverse one.
 template <typename R>
 sgp_status emit_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
-  const auto seq = scheme_seq(scheme);
-  SGP_TRY(x_pass<R>(c, XP_NL | XP_FWD, seq[0].second * dt, 0.0));
-  const int inner = (int)seq.size();
-  for (long long s = 0; s < nsteps; ++s) {
-    const double toff = (double)s * dt;   // offset of this step's start
-    double sub = 0.0;                     // time advanced within the step
-    for (int k = 1; k < inner; ++k) {
-      if (seq[k].first == 'L') {
-        SGP_TRY(linear_middle<R>(c, seq[k].second * dt));
-        sub += seq[k].second;
-      } else {
-        double coef = seq[k].second;
-        const bool last_in_step = (k == inner - 1);
-        const bool last = last_in_step && (s == nsteps - 1);
-        if (last_in_step && !last) coef += seq[0].second;   // merge with the next step's first N
-        const double tn = last_in_step ? (double)(s + 1) * dt : toff + sub * dt;
-        const int mode = last ? (XP_INV | XP_NL) : (XP_INV | XP_NL | XP_FWD);
-        SGP_TRY(x_pass<R>(c, mode, coef * dt, tn));
-      }
+  const std::vector<SubRec> subs = merged_substeps(scheme, nsteps, dt);
+  bool xspec = false;
+  for (size_t j = 0; j < subs.size(); ++j) {
+    if (subs[j].kind == 'N') {
+      int mode = XP_NL | (xspec ? XP_INV : 0);
+      xspec = (j + 1 < subs.size());
+      if (xspec) mode |= XP_FWD;
+      SGP_TRY(x_pass<R>(c, mode, subs[j].delta, subs[j].toff));
+    } else {
+      if (!xspec) SGP_TRY(x_pass<R>(c, XP_FWD, 0.0, 0.0));
+      xspec = true;
+      SGP_TRY(linear_middle<R>(c, subs[j].delta));
     }
   }
+  if (xspec) SGP_TRY(x_pass<R>(c, XP_INV, 0.0, 0.0));
   c->launches++;
   {
     ProfScope ps(c, PK_OTHER);
@@ -563,13 +602,14 @@ sgp_status emit_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   return SGP_OK;
 }
 
-// Tables for every substep size of the scheme (before a capture).
+// Tables for every linear substep size a run of the scheme uses, merged ones
+// included (before a capture).
 template <typename R>
 sgp_status ensure_tables(sgp_ctx* c, double dt, int scheme) {
-  for (auto& st : scheme_seq(scheme))
-    if (st.first == 'L') {
+  for (auto& st : merged_substeps(scheme, 3, dt))
+    if (st.kind == 'L') {
       const LinTables* t = nullptr;
-      SGP_TRY(get_tables<R>(c, st.second * dt, &t));
+      SGP_TRY(get_tables<R>(c, st.delta, &t));
     }
   return SGP_OK;
 }
@@ -604,11 +644,23 @@ sgp_status get_graph(sgp_ctx* c, long long steps, double dt, int scheme, cudaGra
   return SGP_OK;
 }
 
-// Launches issued by one chunk of `steps` steps (for the launch counter).
+// Launches issued by one chunk of `steps` steps (for the launch counter):
+// the pass count of emit_steps plus the time update.
 long long chunk_launches(const sgp_ctx* c, long long steps, int scheme) {
-  const long long lin = (scheme == SGP_TS2 ? 1 : 3) * steps;
   const long long per_l = c->dim == 2 ? 1 : 3;
-  return lin * per_l + lin + 1 + 1;
+  long long n = 1;
+  bool xspec = false;
+  const std::vector<SubRec> subs = merged_substeps(scheme, steps, 1.0);
+  for (size_t j = 0; j < subs.size(); ++j) {
+    if (subs[j].kind == 'N') {
+      n += 1;
+      xspec = (j + 1 < subs.size());
+    } else {
+      n += (xspec ? 0 : 1) + per_l;
+      xspec = true;
+    }
+  }
+  return n + (xspec ? 1 : 0);
 }
 
 template <typename R>
@@ -780,37 +832,9 @@ sgp_status adjoint_linear(sgp_ctx* c, const void* phi, double delta) {
   return x_pass_on<R>(c, r.g, XP_INV, 0.0, 0.0);
 }
 
-struct SubRec {
-  char kind;
-  double delta;
-  double toff;     // time of the substep relative to the segment start
-};
-
-// Substeps of n steps of the scheme from a segment start, with the
-// nonlinear substeps that meet at a step boundary merged (same time; the
-// flow of Eq. (solution2) over a then b is the flow over a + b).  The time
-// of the substep at the end of step s is (s + 1) dt, as in the step path.
+// Substeps of a recomputed segment of n steps (times relative to its start).
 std::vector<SubRec> segment_substeps(int scheme, long long n, double dt) {
-  const auto seq = scheme_seq(scheme);
-  std::vector<SubRec> subs;
-  for (long long s = 0; s < n; ++s) {
-    double sub = 0.0;
-    for (size_t k = 0; k < seq.size(); ++k) {
-      const double delta = seq[k].second * dt;
-      if (seq[k].first == 'L') {
-        subs.push_back({'L', delta, (double)s * dt + sub * dt});
-        sub += seq[k].second;
-        continue;
-      }
-      const double toff = (k == seq.size() - 1) ? (double)(s + 1) * dt
-                                                  : (double)s * dt + sub * dt;
-      if (k == 0 && !subs.empty() && subs.back().kind == 'N')
-        subs.back().delta += delta;        // meets the previous step's last N
-      else
-        subs.push_back({'N', delta, toff});
-    }
-  }
-  return subs;
+  return merged_substeps(scheme, n, dt);
 }
 
 // One segment: recompute the states from seg[0] substep by substep, then
@@ -899,11 +923,11 @@ sgp_status backward_sweep(sgp_ctx* c) {
   const size_t part_bytes = (size_t)c->batch * nblocks * GP_N * sizeof(double);
   SGP_TRY(ensure_buf(c, (void**)&r.part, &r.part_cap, part_bytes));
   SGP_CUDA(c, cudaMemsetAsync(r.part, 0, part_bytes, c->stream));
-  for (const auto& st : seq)
-    if (st.first == 'L') {
+  for (const auto& st : merged_substeps(r.scheme, std::min<long long>(r.interval, 3), r.dt))
+    if (st.kind == 'L') {       // tables of the forward and the reversed linear substeps
       const LinTables* t = nullptr;
-      SGP_TRY(get_tables<R>(c, st.second * r.dt, &t));
-      SGP_TRY(get_tables<R>(c, -st.second * r.dt, &t));
+      SGP_TRY(get_tables<R>(c, st.delta, &t));
+      SGP_TRY(get_tables<R>(c, -st.delta, &t));
     }
   const std::vector<SubRec> full = segment_substeps(r.scheme, r.interval, r.dt);
   const bool graphs = c->use_graphs && !c->profiling;
@@ -1422,7 +1446,7 @@ sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   if (!c) return SGP_EINVAL;
   if (nsteps < 0) return fail(c, SGP_EINVAL, "nsteps < 0");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SGP_EINVAL, "dt must be positive and finite");
-  if (scheme != SGP_TS2 && scheme != SGP_TS4) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
+  if (!valid_scheme(scheme)) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
   if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_step before sgp_set_state");
   if (nsteps == 0) return SGP_OK;
   DeviceGuard guard(c->device);
@@ -1436,7 +1460,7 @@ sgp_status sgp_record(sgp_ctx* c, long long nsteps, double dt, int scheme, long 
   if (nsteps <= 0) return fail(c, SGP_EINVAL, "nsteps must be positive");
   if (interval < 0) return fail(c, SGP_EINVAL, "interval < 0");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SGP_EINVAL, "dt must be positive and finite");
-  if (scheme != SGP_TS2 && scheme != SGP_TS4) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
+  if (!valid_scheme(scheme)) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
   if (!c->have_state) return fail(c, SGP_ESTATE, "sgp_record before sgp_set_state");
   DeviceGuard guard(c->device);
   return c->prec == SGP_F32 ? record_steps<float>(c, nsteps, dt, scheme, interval)
@@ -1875,7 +1899,7 @@ sgp_status sgp_ensemble_step(sgp_ens* e, long long nsteps, double dt, int scheme
   if (!e) return SGP_EINVAL;
   if (nsteps < 0) return efail(e, SGP_EINVAL, "nsteps < 0");
   if (!(dt > 0.0) || !std::isfinite(dt)) return efail(e, SGP_EINVAL, "dt must be positive and finite");
-  if (scheme != SGP_TS2 && scheme != SGP_TS4) return efail(e, SGP_EINVAL, "unknown scheme %d", scheme);
+  if (!valid_scheme(scheme)) return efail(e, SGP_EINVAL, "unknown scheme %d", scheme);
   if (!e->have_state) return efail(e, SGP_ESTATE, "sgp_ensemble_step before any member state");
   if (nsteps == 0) return SGP_OK;
   DeviceGuard guard(e->device);

@@ -21,9 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgp.so")
 
 SGP_F32, SGP_F64 = 32, 64
-SGP_TS2, SGP_TS4 = 0, 1
+SGP_TS2, SGP_TS4, SGP_TS2_LNL, SGP_TS4_LOUTER = 0, 1, 2, 3
 SGP_SUB_NONLINEAR, SGP_SUB_LINEAR = 0, 1
-SCHEMES = {"ts2": SGP_TS2, "ts4": SGP_TS4}
+SCHEMES = {"ts2": SGP_TS2, "ts4": SGP_TS4, "ts2_lnl": SGP_TS2_LNL, "ts4_l": SGP_TS4_LOUTER}
 PRECS = {"f32": SGP_F32, "f64": SGP_F64}
 
 

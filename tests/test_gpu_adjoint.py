@@ -69,7 +69,8 @@ def _run_adjoint(n, L, prm, psi0, dt, nsteps, scheme, prec, c, w, interval=0):
 PRM_SMALL = O.Params(omega=0.6, gamma=1.0, c0=400.0, c1=-3.0, c2=5.0, gx=1.0, gy=1.3)
 
 
-@pytest.mark.parametrize("scheme,nsteps,interval", [("ts2", 6, 0), ("ts4", 4, 3), ("ts2", 5, 1)])
+@pytest.mark.parametrize("scheme,nsteps,interval", [("ts2", 6, 0), ("ts4", 4, 3), ("ts2", 5, 1),
+                                                     ("ts2_lnl", 5, 2), ("ts4_l", 4, 3)])
 def test_adjoint_fp64_matches_oracle_fd(scheme, nsteps, interval):
     n, L, dt = (16, 16), 8.0, 2e-3
     psi0 = inputs.gaussian_random_phase(n, L, seed=11, amp=0.3)

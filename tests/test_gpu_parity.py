@@ -323,3 +323,41 @@ def test_fp32_mass_drift_on_radix3_lengths(n, L):
     m1 = c.observables()[0]["mass"]
     c.close()
     assert abs(m1 / m0 - 1) < 5e-6
+
+
+# ----------------------------------------------------------------------------
+# compositions with the linear flow outside (Sec. 3.3, the other reading)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", ["ts2_lnl", "ts4_l"])
+@pytest.mark.parametrize("n,L", [((64, 48), (8.0, 6.0)), ((96, 64), (9.0, 8.0))])
+def test_linear_outer_schemes_f64(scheme, n, L):
+    prm = _params(omega=0.6, gamma=1.1, gx=1.0, gy=1.3, c1=-2.0, c2=3.0)
+    psi = inputs.gaussian_random_phase(n, L, seed=21, amp=0.5)
+    out, t = _gpu_run(n, L, prm, psi, 20, 2e-3, scheme, "f64")
+    ref, tr = _oracle_run(n, L, prm, psi, 20, 2e-3, scheme)
+    assert abs(t - tr) < 1e-14
+    assert O.rel_l2(out, ref) < 1e-10
+
+
+@pytest.mark.parametrize("scheme", ["ts2_lnl", "ts4_l"])
+def test_linear_outer_schemes_3d_and_f32(scheme):
+    n, L = (32, 32, 48), (5.0, 5.0, 6.0)
+    prm = _params(omega=0.5, gamma=0.8, gz=1.5)
+    psi = inputs.gaussian_random_phase(n, L, seed=22, amp=0.5)
+    ref, _ = _oracle_run(n, L, prm, psi, 10, 2e-3, scheme)
+    out64, _ = _gpu_run(n, L, prm, psi, 10, 2e-3, scheme, "f64")
+    assert O.rel_l2(out64, ref) < 1e-10
+    out32, _ = _gpu_run(n, L, prm, psi, 10, 2e-3, scheme, "f32")
+    assert O.rel_l2(out32, ref) < 1e-5
+
+
+@pytest.mark.parametrize("scheme", ["ts2_lnl", "ts4_l"])
+def test_linear_outer_schemes_graph_replay(scheme):
+    """200 steps (graph replays of 64-step chunks, where the chunks meet the
+    linear substeps are not merged) against the oracle."""
+    n, L = (48, 48), 6.0
+    prm = _params(omega=0.4, gamma=0.9)
+    psi = inputs.gaussian_random_phase(n, L, seed=23, amp=0.5)
+    out, _ = _gpu_run(n, L, prm, psi, 200, 1e-3, scheme, "f64")
+    ref, _ = _oracle_run(n, L, prm, psi, 200, 1e-3, scheme)
+    assert O.rel_l2(out, ref) < 1e-10
