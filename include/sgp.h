@@ -41,6 +41,8 @@
 #ifndef SGP_H
 #define SGP_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -69,6 +71,12 @@ typedef enum { SGP_F32 = 32, SGP_F64 = 64 } sgp_prec;
  * TS4_LOUTER: L(a1 tau) N(b1 tau) L(a2 tau) N(b2 tau) L(a2 tau) N(b1 tau)
  * L(a1 tau).  Time advances in the L substeps. */
 typedef enum { SGP_TS2 = 0, SGP_TS4 = 1, SGP_TS2_LNL = 2, SGP_TS4_LOUTER = 3 } sgp_scheme;
+
+/* Caller-supplied device allocator (optional).  alloc returns a device
+ * pointer of at least `bytes` bytes on `device` (usable on the context
+ * stream `stream`), or NULL on failure; free releases such a pointer. */
+typedef void* (*sgp_alloc_fn)(size_t bytes, int device, void* stream, void* user);
+typedef void (*sgp_free_fn)(void* ptr, int device, void* stream, void* user);
 
 /* Flags of sgp_autotune. */
 enum { SGP_TUNE_FORCE = 1 };
@@ -131,6 +139,17 @@ sgp_status sgp_set_params(sgp_ctx* ctx, const sgp_params* p);
  * linear-flow tables are built per member.  Same synchronisation and errors
  * as sgp_set_params, plus SGP_EINVAL for count != batch. */
 sgp_status sgp_set_params_batch(sgp_ctx* ctx, const sgp_params* p, int count);
+
+/* Device memory of the contexts (and ensemble groups) created after this
+ * call comes from `alloc` and goes back through `free_fn`: the field, the
+ * twiddle and mode tables, the observables scratch, the adjoint checkpoints
+ * and the autotuner's scratch.  Each context keeps the pair it was created
+ * with until sgp_destroy; frees synchronise the context stream first.
+ * alloc = free_fn = NULL restores cudaMalloc/cudaFree.  Process-wide, not
+ * thread-safe against concurrent sgp_create_grid.  An allocation failure
+ * makes the calling entry point return SGP_ENOMEM or SGP_ECUDA.  Errors:
+ * SGP_EINVAL if exactly one of the two functions is NULL. */
+sgp_status sgp_set_allocator(sgp_alloc_fn alloc, sgp_free_fn free_fn, void* user);
 
 /* Copy a field into the context and set the time to t0.  `src` holds
  * batch*5*nz*ny*nx complex elements of the context precision in the layout

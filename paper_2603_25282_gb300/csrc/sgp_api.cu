@@ -234,6 +234,15 @@ struct AdjRec {
   const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
+// Device allocator of a context: the caller's (sgp_set_allocator) or
+// cudaMalloc/cudaFree when none was set.
+struct Allocator {
+  sgp_alloc_fn alloc = nullptr;
+  sgp_free_fn free = nullptr;
+  void* user = nullptr;
+};
+Allocator g_allocator;     // for contexts created from now on
+
 }  // namespace
 
 struct sgp_ctx {
@@ -270,12 +279,34 @@ struct sgp_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
   std::vector<cudaEvent_t> event_pool;
   AdjRec adj;
+  Allocator alloc;                  // taken from g_allocator at creation
   std::string err;
 };
 
 namespace {
 
 std::string g_create_err;
+
+cudaError_t dev_alloc(sgp_ctx* c, void** p, size_t bytes) {
+  if (c->alloc.alloc) {
+    *p = c->alloc.alloc(bytes, c->device, (void*)c->stream, c->alloc.user);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+// Frees a buffer of the context.  With the caller's allocator the context
+// stream is synchronised first (a pooled block may be handed out again at
+// once); cudaFree synchronises by itself.
+void dev_free(sgp_ctx* c, void* p) {
+  if (!p) return;
+  if (c->alloc.free) {
+    cudaStreamSynchronize(c->stream);
+    c->alloc.free(p, c->device, (void*)c->stream, c->alloc.user);
+  } else {
+    cudaFree(p);
+  }
+}
 
 sgp_status fail(sgp_ctx* c, sgp_status s, const char* fmt, ...) {
   char buf[512];
@@ -367,8 +398,8 @@ void free_tables(sgp_ctx* c) {
     c->adj.graph = nullptr;
   }
   for (auto& t : c->tables) {
-    cudaFree(t.mt);
-    cudaFree(t.kz);
+    dev_free(c, t.mt);
+    dev_free(c, t.kz);
   }
   c->tables.clear();
 }
@@ -406,8 +437,8 @@ sgp_status get_tables(sgp_ctx* c, double delta, const LinTables** out) {
   const int NX = c->n[0], NY = c->n[1], NZ = c->n[2];
   const size_t nent = (size_t)(NX / 2 + 1) * (NY / 2 + 1);
   const int ntab = c->shared_lin ? 1 : c->batch;
-  SGP_CUDA(c, cudaMalloc(&t.mt, nent * MT_STRIDE * sizeof(R) * ntab));
-  SGP_CUDA(c, cudaMalloc(&t.kz, (size_t)NZ * sizeof(cplx<R>)));
+  SGP_CUDA(c, dev_alloc(c, &t.mt, nent * MT_STRIDE * sizeof(R) * ntab));
+  SGP_CUDA(c, dev_alloc(c, &t.kz, (size_t)NZ * sizeof(cplx<R>)));
   const int work = (int)std::max<size_t>(nent, (size_t)NZ);
   {
     ProfScope ps(c, PK_TAB);
@@ -709,10 +740,10 @@ size_t state_bytes(const sgp_ctx* c) { return (size_t)c->batch * 5 * c->ntot * c
 sgp_status ensure_buf(sgp_ctx* c, void** p, size_t* cap, size_t bytes) {
   if (*cap >= bytes && *p) return SGP_OK;
   SGP_CUDA(c, cudaStreamSynchronize(c->stream));
-  cudaFree(*p);
+  dev_free(c, *p);
   *p = nullptr;
   *cap = 0;
-  SGP_CUDA(c, cudaMalloc(p, bytes));
+  SGP_CUDA(c, dev_alloc(c, p, bytes));
   *cap = bytes;
   return SGP_OK;
 }
@@ -720,13 +751,13 @@ sgp_status ensure_buf(sgp_ctx* c, void** p, size_t* cap, size_t bytes) {
 void free_adj(sgp_ctx* c) {
   AdjRec& r = c->adj;
   if (r.graph) cudaGraphExecDestroy(r.graph);
-  cudaFree(r.ckpt);
-  cudaFree(r.seg);
-  cudaFree(r.g);
-  cudaFree(r.spec);
-  cudaFree(r.dp);
-  cudaFree(r.part);
-  cudaFree(r.lab);
+  dev_free(c, r.ckpt);
+  dev_free(c, r.seg);
+  dev_free(c, r.g);
+  dev_free(c, r.spec);
+  dev_free(c, r.dp);
+  dev_free(c, r.part);
+  dev_free(c, r.lab);
   r = AdjRec();
 }
 
@@ -1032,7 +1063,7 @@ sgp_status use_variant(sgp_ctx* c, int a, int v) {
     return fail(c, SGP_EINVAL, "variant %d does not exist for N = %d on axis %d", v, c->n[a], a);
   if (v == 3 && !c->tw4[a]) {
     SGP_CUDA(c, cudaStreamSynchronize(c->stream));
-    SGP_CUDA(c, cudaMalloc(&c->tw4[a], (size_t)c->n[a] * sizeof(TwE<float>)));
+    SGP_CUDA(c, dev_alloc(c, &c->tw4[a], (size_t)c->n[a] * sizeof(TwE<float>)));
     k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], 4, (TwE<float>*)c->tw4[a]);
     c->launches++;
     SGP_CUDA(c, cudaGetLastError());
@@ -1077,7 +1108,7 @@ sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
   const size_t sb = state_bytes(c);
   void* scratch = nullptr;
   SGP_CUDA(c, cudaStreamSynchronize(c->stream));
-  SGP_CUDA(c, cudaMalloc(&scratch, sb));
+  SGP_CUDA(c, dev_alloc(c, &scratch, sb));
   SGP_CUDA(c, cudaMemcpyAsync(scratch, c->field, sb, cudaMemcpyDeviceToDevice, c->stream));
   std::swap(c->field, scratch);            // the steps below advance the copy
   const double dt = 1e-3;
@@ -1122,7 +1153,7 @@ sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
   cudaEventDestroy(e1);
   cudaStreamSynchronize(c->stream);
   std::swap(c->field, scratch);
-  cudaFree(scratch);
+  dev_free(c, scratch);
   if (st == SGP_OK) tune_cache()[tune_key(c)] = std::vector<int>(best, best + 3);
   return st;
 }
@@ -1266,6 +1297,17 @@ extern "C" {
 
 int sgp_version(void) { return 200; }
 
+sgp_status sgp_set_allocator(sgp_alloc_fn alloc, sgp_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    g_create_err = "allocator and free function must be given together";
+    return SGP_EINVAL;
+  }
+  g_allocator.alloc = alloc;
+  g_allocator.free = free_fn;
+  g_allocator.user = user;
+  return SGP_OK;
+}
+
 const char* sgp_status_string(sgp_status s) {
   switch (s) {
     case SGP_OK: return "SGP_OK";
@@ -1297,6 +1339,7 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
     return fail(nullptr, SGP_EINVAL, "CUDA device %d not available", device);
   DeviceGuard guard(device);
   sgp_ctx* c = new sgp_ctx();
+  c->alloc = g_allocator;
   c->dim = dim;
   for (int a = 0; a < 3; ++a) {
     c->n[a] = a < dim ? n[a] : 1;
@@ -1331,12 +1374,12 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
     if (e != cudaSuccess) return bail(SGP_ECUDA, "kernel attributes", e);
   }
   const size_t fbytes = (size_t)batch * 5 * c->ntot * c->elem;
-  if ((e = cudaMalloc(&c->field, fbytes)) != cudaSuccess)
+  if ((e = dev_alloc(c, &c->field, fbytes)) != cudaSuccess)
     return bail(SGP_ENOMEM, "field allocation", e);
   if ((e = cudaMemsetAsync(c->field, 0, fbytes, c->stream)) != cudaSuccess)
     return bail(SGP_ECUDA, "field clear", e);
   for (int a = 0; a < dim; ++a) {
-    if ((e = cudaMalloc(&c->tw[a], (size_t)c->n[a] * 16)) != cudaSuccess)
+    if ((e = dev_alloc(c, &c->tw[a], (size_t)c->n[a] * 16)) != cudaSuccess)
       return bail(SGP_ENOMEM, "twiddle allocation", e);
     const int E = elems_for(c->n[a], prec);
     if (prec == SGP_F32)
@@ -1345,9 +1388,9 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
       k_twiddles_f64<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], E, (TwE<double>*)c->tw[a]);
     c->launches++;
   }
-  if ((e = cudaMalloc(&c->t_dev, sizeof(double))) != cudaSuccess)
+  if ((e = dev_alloc(c, (void**)&c->t_dev, sizeof(double))) != cudaSuccess)
     return bail(SGP_ENOMEM, "time allocation", e);
-  if ((e = cudaMalloc(&c->mp_dev, sizeof(MemberPrm) * batch)) != cudaSuccess)
+  if ((e = dev_alloc(c, (void**)&c->mp_dev, sizeof(MemberPrm) * batch)) != cudaSuccess)
     return bail(SGP_ENOMEM, "parameter allocation", e);
   // observables scratch: the largest per-kernel partial array
   const PassGeom gx = prec == SGP_F32 ? xpass_geom<float>(c->n[0]) : xpass_geom<double>(c->n[0]);
@@ -1359,9 +1402,9 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
     need = std::max(need, tiles * planes * OBL_NT);
   }
   c->partials_len = need * batch;
-  if ((e = cudaMalloc(&c->partials, c->partials_len * sizeof(double))) != cudaSuccess)
+  if ((e = dev_alloc(c, (void**)&c->partials, c->partials_len * sizeof(double))) != cudaSuccess)
     return bail(SGP_ENOMEM, "observables scratch", e);
-  if ((e = cudaMalloc(&c->obs_dev, (size_t)batch * OB_NT * sizeof(double))) != cudaSuccess)
+  if ((e = dev_alloc(c, (void**)&c->obs_dev, (size_t)batch * OB_NT * sizeof(double))) != cudaSuccess)
     return bail(SGP_ENOMEM, "observables output", e);
   if ((e = cudaMemsetAsync(c->obs_dev, 0, (size_t)batch * OB_NT * sizeof(double), c->stream)) !=
       cudaSuccess)
@@ -1605,13 +1648,13 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   free_graphs(c);
   free_tables(c);
   free_adj(c);
-  cudaFree(c->field);
-  for (void* t : c->tw) cudaFree(t);
-  for (void* t : c->tw4) cudaFree(t);
-  cudaFree(c->t_dev);
-  cudaFree(c->mp_dev);
-  cudaFree(c->partials);
-  cudaFree(c->obs_dev);
+  dev_free(c, c->field);
+  for (void* t : c->tw) dev_free(c, t);
+  for (void* t : c->tw4) dev_free(c, t);
+  dev_free(c, c->t_dev);
+  dev_free(c, c->mp_dev);
+  dev_free(c, c->partials);
+  dev_free(c, c->obs_dev);
   recycle_events(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->stream);

@@ -55,6 +55,12 @@ class Obs(ctypes.Structure):
 
 _lib = None
 
+# caller allocator callbacks (sgp_set_allocator)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                            ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_keep = None      # the registered callbacks must outlive their use
+
 
 def lib():
     """Load libsgp.so once (raises if it is missing)."""
@@ -99,6 +105,7 @@ def lib():
         "sgp_destroy": (I, [P]),
         "sgp_observables_static": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                        I, I, ctypes.POINTER(Params), D, P, I, P, ctypes.POINTER(Obs)]),
+        "sgp_set_allocator": (I, [ALLOC_FN, FREE_FN, P]),
         "sgp_variant_exists": (I, [I, I, I]),
         "sgp_set_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
         "sgp_get_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
@@ -167,6 +174,31 @@ def create_grid(n, L, batch=1, prec="f32", device=0, stream=None):
 def _params(kw):
     return Params(**{k: float(kw.get(k, 1.0 if k in ("gx", "gy", "gz") else 0.0))
                      for k, _ in Params._fields_})
+
+
+def use_torch_allocator(enable=True):
+    """sgp_set_allocator with PyTorch's caching allocator (contexts created
+    afterwards take their device memory from torch's pool; it shows in
+    torch.cuda.memory_allocated).  enable=False restores cudaMalloc."""
+    global _allocator_keep
+    if not enable:
+        _check(lib().sgp_set_allocator(ALLOC_FN(), FREE_FN(), None), None)
+        _allocator_keep = None
+        return
+    import torch
+
+    def _alloc(size, device, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), int(device), int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, device, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    keep = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib().sgp_set_allocator(keep[0], keep[1], None), None)
+    _allocator_keep = keep
 
 
 def set_params(ctx, **kw):
