@@ -57,7 +57,8 @@ typedef enum {
   SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up            */
   SGP_ENONFINITE = 5,    /* a NaN/Inf was detected in the observables     */
   SGP_ESTATE = 6,        /* call out of order (e.g. step before set_state)*/
-  SGP_EUNSUPPORTED = 7   /* valid request this build does not implement   */
+  SGP_EUNSUPPORTED = 7,  /* valid request this build does not implement   */
+  SGP_EDRIFT = 8         /* the health check saw the mass drift too far   */
 } sgp_status;
 
 typedef enum { SGP_F32 = 32, SGP_F64 = 64 } sgp_prec;
@@ -200,6 +201,19 @@ sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
  * Errors: SGP_EINVAL for nsteps < 0, dt <= 0 or non-finite dt; SGP_ESTATE
  * before sgp_set_state; SGP_ECUDA if a launch fails. */
 sgp_status sgp_step(sgp_ctx* ctx, long long nsteps, double dt, int scheme);
+
+/* Health check of sgp_step (off by default).  With every > 0, sgp_step
+ * runs in chunks of at most `every` steps and after each chunk sums every
+ * member's mass h^d sum |phi|^2 in FP64 on the device (Sec. 2: the scheme
+ * conserves it exactly) and compares it with the mass at the last
+ * sgp_set_state (taken at the first checked step after it).  It returns
+ * SGP_ENONFINITE if a mass is NaN or Inf and SGP_EDRIFT if |m/m0 - 1| >
+ * drift_tol for some member, with the member, its mass and the step count
+ * in sgp_last_error; the steps up to that check have been taken and the
+ * time advanced accordingly.  Each check synchronises the context stream.
+ * every = 0 turns the check off.  Errors: SGP_EINVAL for every < 0 or a
+ * negative or non-finite drift_tol. */
+sgp_status sgp_set_health_check(sgp_ctx* ctx, long long every, double drift_tol);
 
 /* Enable (default) or disable graph replay in sgp_step. */
 sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);

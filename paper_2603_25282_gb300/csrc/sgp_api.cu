@@ -279,6 +279,12 @@ struct sgp_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
   std::vector<cudaEvent_t> event_pool;
   AdjRec adj;
+  // health check of sgp_step
+  long long health_every = 0;
+  double health_tol = 0.0;
+  bool health_ref = false;          // m0 holds the mass at the last set_state
+  std::vector<double> m0;
+  double* mass_dev = nullptr;       // [batch] + partials
   Allocator alloc;                  // taken from g_allocator at creation
   std::string err;
 };
@@ -1045,6 +1051,81 @@ sgp_status state_lab(sgp_ctx* c, void* dst, int on_device) {
 }
 
 // ----------------------------------------------------------------------------
+// health check: per-member mass in FP64 (Sec. 2)
+// ----------------------------------------------------------------------------
+constexpr int kMassBlocks = 64;
+
+template <typename R>
+__global__ void k_mass(const cplx<R>* f, long long n, double* part) {
+  const int m = blockIdx.y;
+  const cplx<R>* b = f + (size_t)m * n;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cplx<R> v = b[i];
+    s += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+  }
+  __shared__ double red[8];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[(size_t)m * kMassBlocks + blockIdx.x] = t;
+  }
+}
+
+// masses of all members into out[batch] (synchronises)
+template <typename R>
+sgp_status member_mass(sgp_ctx* c, std::vector<double>& out) {
+  if (!c->mass_dev)
+    SGP_CUDA(c, dev_alloc(c, (void**)&c->mass_dev, sizeof(double) * c->batch * (kMassBlocks + 1)));
+  double* part = c->mass_dev + c->batch;
+  c->launches += 2;
+  k_mass<R><<<dim3(kMassBlocks, c->batch), 256, 0, c->stream>>>((const cplx<R>*)c->field,
+                                                                 5 * c->ntot, part);
+  k_reduce_partials<<<(c->batch + 127) / 128, 128, 0, c->stream>>>(part, kMassBlocks, 1, c->batch,
+                                                                   c->mass_dev, 1, 0);
+  SGP_CUDA(c, cudaGetLastError());
+  out.resize(c->batch);
+  SGP_CUDA(c, cudaMemcpyAsync(out.data(), c->mass_dev, sizeof(double) * c->batch,
+                              cudaMemcpyDeviceToHost, c->stream));
+  SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double cell = c->h[0] * c->h[1] * (c->dim == 3 ? c->h[2] : 1.0);
+  for (double& v : out) v *= cell;
+  return SGP_OK;
+}
+
+// sgp_step with the health check: chunks of health_every steps, each
+// followed by the mass comparison
+template <typename R>
+sgp_status checked_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
+  if (!c->health_ref) {
+    SGP_TRY(member_mass<R>(c, c->m0));
+    c->health_ref = true;
+  }
+  std::vector<double> m;
+  long long done = 0;
+  while (done < nsteps) {
+    const long long n = std::min(c->health_every, nsteps - done);
+    SGP_TRY(run_steps<R>(c, n, dt, scheme));
+    done += n;
+    SGP_TRY(member_mass<R>(c, m));
+    for (int k = 0; k < c->batch; ++k) {
+      if (!std::isfinite(m[k]))
+        return fail(c, SGP_ENONFINITE, "member %d: mass %g after %lld of %lld steps", k, m[k],
+                    done, nsteps);
+      const double drift = std::fabs(m[k] / c->m0[k] - 1.0);
+      if (!(drift <= c->health_tol))
+        return fail(c, SGP_EDRIFT, "member %d: mass %.17g drifted %.3e from %.17g after %lld of %lld steps",
+                    k, m[k], drift, c->m0[k], done, nsteps);
+    }
+  }
+  return SGP_OK;
+}
+
+// ----------------------------------------------------------------------------
 // kernel variants: plan and autotuner
 // ----------------------------------------------------------------------------
 void drop_graphs(sgp_ctx* c) {
@@ -1318,6 +1399,7 @@ const char* sgp_status_string(sgp_status s) {
     case SGP_ENONFINITE: return "SGP_ENONFINITE";
     case SGP_ESTATE: return "SGP_ESTATE";
     case SGP_EUNSUPPORTED: return "SGP_EUNSUPPORTED";
+    case SGP_EDRIFT: return "SGP_EDRIFT";
   }
   return "unknown";
 }
@@ -1453,6 +1535,7 @@ sgp_status sgp_set_state(sgp_ctx* c, const void* src, int src_on_device, double 
                               c->stream));
   if (!src_on_device) SGP_CUDA(c, cudaStreamSynchronize(c->stream));
   c->adj.valid = false;
+  c->health_ref = false;
   c->t = t0;
   c->have_state = true;
   return SGP_OK;
@@ -1494,8 +1577,21 @@ sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   if (nsteps == 0) return SGP_OK;
   DeviceGuard guard(c->device);
   c->adj.valid = false;
+  if (c->health_every > 0)
+    return c->prec == SGP_F32 ? checked_steps<float>(c, nsteps, dt, scheme)
+                              : checked_steps<double>(c, nsteps, dt, scheme);
   return c->prec == SGP_F32 ? run_steps<float>(c, nsteps, dt, scheme)
                             : run_steps<double>(c, nsteps, dt, scheme);
+}
+
+sgp_status sgp_set_health_check(sgp_ctx* c, long long every, double drift_tol) {
+  if (!c) return SGP_EINVAL;
+  if (every < 0) return fail(c, SGP_EINVAL, "every < 0");
+  if (!(drift_tol >= 0.0) || !std::isfinite(drift_tol))
+    return fail(c, SGP_EINVAL, "drift_tol must be finite and >= 0");
+  c->health_every = every;
+  c->health_tol = drift_tol;
+  return SGP_OK;
 }
 
 sgp_status sgp_record(sgp_ctx* c, long long nsteps, double dt, int scheme, long long interval) {
@@ -1655,6 +1751,7 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   dev_free(c, c->mp_dev);
   dev_free(c, c->partials);
   dev_free(c, c->obs_dev);
+  dev_free(c, c->mass_dev);
   recycle_events(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->stream);

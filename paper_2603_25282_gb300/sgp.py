@@ -106,6 +106,7 @@ def lib():
         "sgp_observables_static": (I, [I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                        I, I, ctypes.POINTER(Params), D, P, I, P, ctypes.POINTER(Obs)]),
         "sgp_set_allocator": (I, [ALLOC_FN, FREE_FN, P]),
+        "sgp_set_health_check": (I, [P, LL, D]),
         "sgp_variant_exists": (I, [I, I, I]),
         "sgp_set_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
         "sgp_get_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
@@ -210,6 +211,11 @@ def set_params_batch(ctx, plist):
     """Per-member parameters: plist is a list of dicts (one per member)."""
     arr = (Params * len(plist))(*[_params(d) for d in plist])
     _check(lib().sgp_set_params_batch(ctx, arr, len(plist)), ctx)
+
+
+def set_health_check(ctx, every, drift_tol):
+    """sgp_set_health_check: mass checked every `every` steps of sgp_step."""
+    _check(lib().sgp_set_health_check(ctx, int(every), float(drift_tol)), ctx)
 
 
 def set_graphs(ctx, enable):
@@ -379,6 +385,9 @@ class Context:
 
     def set_graphs(self, enable):
         set_graphs(self.handle, enable)
+
+    def set_health_check(self, every, drift_tol):
+        set_health_check(self.handle, every, drift_tol)
 
     def set_state(self, src, t0=0.0):
         set_state(self.handle, src, self.dtype, t0)

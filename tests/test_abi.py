@@ -36,6 +36,7 @@ def test_version_and_status_strings(lib):
     assert lib.sgp_version() >= 100
     assert lib.sgp_status_string(0) == b"SGP_OK"
     assert lib.sgp_status_string(1) == b"SGP_EINVAL"
+    assert lib.sgp_status_string(8) == b"SGP_EDRIFT"
 
 
 def test_create_grid_rejects_bad_arguments_before_cuda(lib):
@@ -55,6 +56,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.sgp_step(None, 1, 0.1, 0) == 1
     assert lib.sgp_observables(None, None) == 1
     assert lib.sgp_record(None, 10, 0.1, 0, 0) == 1
+    assert lib.sgp_set_health_check(None, 10, 1e-6) == 1
     # allocator and free function come together
     assert lib.sgp_set_allocator(sgp.ALLOC_FN(lambda *a: None), sgp.FREE_FN(), None) == 1
     assert lib.sgp_set_allocator(sgp.ALLOC_FN(), sgp.FREE_FN(), None) == 0

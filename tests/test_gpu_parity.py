@@ -361,3 +361,93 @@ def test_linear_outer_schemes_graph_replay(scheme):
     out, _ = _gpu_run(n, L, prm, psi, 200, 1e-3, scheme, "f64")
     ref, _ = _oracle_run(n, L, prm, psi, 200, 1e-3, scheme)
     assert O.rel_l2(out, ref) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# full-size 3D workload, checkpoint/resume, health check
+# ----------------------------------------------------------------------------
+def test_3d_128_full_size_first_steps():
+    """128^3 on [-8,8]^3, Omega = 0.7, gamma = 1, c = (500, -2, 5), gz = 2:
+    the first two TS2 and TS4 steps against the oracle (FP64 within 1e-10,
+    FP32 within 1e-5)."""
+    n, L = (128, 128, 128), 8.0
+    prm = _params(omega=0.7, gamma=1.0, c0=500.0, c1=-2.0, c2=5.0, gz=2.0)
+    psi = inputs.gaussian_random_phase(n, L, seed=4, amp=0.01)
+    for scheme in ("ts2", "ts4"):
+        ref, _ = _oracle_run(n, L, prm, psi, 2, 1e-3, scheme)
+        out64, _ = _gpu_run(n, L, prm, psi, 2, 1e-3, scheme, "f64")
+        assert O.rel_l2(out64, ref) < 1e-10, scheme
+        out32, _ = _gpu_run(n, L, prm, psi, 2, 1e-3, scheme, "f32")
+        assert O.rel_l2(out32, ref) < 1e-5, scheme
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_save_and_resume_is_bitwise(prec, tmp_path):
+    """A run of 150 + 150 TS4 steps in one context equals 150 steps, the
+    state and time saved to a file, a fresh context loaded from it and 150
+    more steps, bit for bit (the resumed context replays the same chunks)."""
+    n, L = (48, 64), (6.0, 8.0)
+    prm = _params(gx=1.1, gy=0.9)
+    dt_ = np.complex64 if prec == "f32" else np.complex128
+    psi = inputs.gaussian_random_phase(n, L, seed=41, amp=0.4)[None].astype(dt_)
+    a = _ctx(n, L, prec, **prm)
+    a.set_state(psi.copy(), 0.0)
+    a.step(150, 1e-3, "ts4")
+    np.save(tmp_path / "state.npy", a.get_state())
+    np.save(tmp_path / "t.npy", np.array([a.t]))
+    a.step(150, 1e-3, "ts4")
+    b = _ctx(n, L, prec, **prm)
+    b.set_state(np.load(tmp_path / "state.npy"), float(np.load(tmp_path / "t.npy")[0]))
+    b.step(150, 1e-3, "ts4")
+    assert b.t == a.t
+    assert np.array_equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
+
+
+def test_health_check_passes_and_matches_unchecked_run():
+    n, L = (64, 64), 8.0
+    prm = _params()
+    psi = inputs.gaussian_random_phase(n, L, seed=42, amp=0.01)[None].astype(np.complex64)
+    outs = []
+    for every in (0, 100):
+        c = _ctx(n, L, "f32", **prm)
+        c.set_health_check(every, 1e-5)
+        c.set_state(psi.copy(), 0.0)
+        c.step(300, 1e-3, "ts4")
+        assert abs(c.t - 0.3) < 1e-14
+        outs.append(c.get_state()[0].astype(np.complex128))
+        c.close()
+    # the chunks of the checked run end and restart the step sequence, so the
+    # two runs differ by FP32 rounding only
+    assert O.rel_l2(outs[0], outs[1]) < 2e-5
+    ref, _ = _oracle_run(n, L, prm, psi[0].astype(np.complex128), 300, 1e-3, "ts4")
+    assert O.rel_l2(outs[1], ref) < 1e-4
+
+
+def test_health_check_reports_nonfinite_and_drift():
+    n, L = (32, 32), 4.0
+    c = _ctx(n, L, "f32", batch=2, **_params())
+    psi = inputs.gaussian_random_phase(n, L, seed=43, amp=0.3).astype(np.complex64)
+    bad = psi.copy()
+    bad[1, 3, 4] = np.nan
+    c.set_health_check(5, 1e-5)
+    c.set_state(np.stack([psi, bad]), 0.0)
+    with pytest.raises(sgp.SgpError, match="ENONFINITE") as e:
+        c.step(20, 1e-3, "ts2")
+    assert "member 1" in str(e.value)
+    # a tolerance of zero: the first check after the first chunk fails
+    # (FP32 rounding moves the mass) and the time has advanced one chunk
+    c.set_health_check(5, 0.0)
+    c.set_state(np.stack([psi, psi]), 0.0)
+    with pytest.raises(sgp.SgpError, match="EDRIFT") as e:
+        c.step(20, 1e-3, "ts2")
+    assert "member 0" in str(e.value)
+    assert abs(c.t - 5e-3) < 1e-15
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        c.set_health_check(-1, 1e-5)
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        c.set_health_check(10, float("nan"))
+    c.set_health_check(0, 0.0)                   # off again
+    c.step(20, 1e-3, "ts2")
+    c.close()
