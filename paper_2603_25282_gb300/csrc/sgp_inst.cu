@@ -155,7 +155,8 @@ template <int N>
 static cudaError_t linepass_prepare_n() {
   constexpr int E = variant_elems<Real, N, V>();
   static int done = -1;
-  cudaError_t e = prepare(k_linepass<Real, N, E, G>, LCfg<Real, N, E, G>::SMEM, &done);
+  cudaError_t e = prepare(k_linepass<Real, N, E, G>,
+                          LCfg<Real, N, E, G>::SMEM + LCfg<Real, N, E, G>::TAB, &done);
 #if SGP_VAR == 0
   if (e != cudaSuccess) return e;
   static int done_o = -1;
@@ -172,7 +173,9 @@ static cudaError_t linepass_n(const LPassArgs<Real>& a, int planes, int members,
   cudaError_t e = linepass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
-  k_linepass<Real, N, E, G><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  // the mode-table slice in shared memory for 2D y-lines with the mix
+  const size_t smem = Cfg::SMEM + (((a.mode & LP_MIX) && a.axis == 1) ? Cfg::TAB : 0);
+  k_linepass<Real, N, E, G><<<grid, Cfg::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

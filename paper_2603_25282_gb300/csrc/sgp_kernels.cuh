@@ -454,6 +454,11 @@ struct LCfg {
   static constexpr int NB = 2;
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(NB * TILE * LP);
   static constexpr int MINB = (THREADS <= 256 && 2 * SMEM <= 220 * 1024) ? 2 : 1;
+  // lines along y in 2D: the tile's slice of the per-mode table (TILE
+  // columns x (N/2 + 1) entries), copied to shared memory asynchronously
+  // at the start so that the mix does not wait on L2 for every mode
+  static constexpr size_t TAB = (size_t)TILE * (N / 2 + 1) * MT_STRIDE * sizeof(R);
+  static_assert(SMEM + TAB <= 227 * 1024, "line pass shared memory");
 };
 
 template <typename R> struct ModeEntry { R khr, khi, am1r, am1i, cm1, sp, bx, by; };
@@ -469,18 +474,53 @@ __device__ __forceinline__ ModeEntry<double> load_mode(const double* mt, int idx
   return ModeEntry<double>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
 }
 
+// the same entry from the shared-memory copy of the table slice
+__device__ __forceinline__ ModeEntry<float> load_mode_shared(const float* t, int idx) {
+  const float4 a = reinterpret_cast<const float4*>(t)[2 * idx];
+  const float4 b = reinterpret_cast<const float4*>(t)[2 * idx + 1];
+  return ModeEntry<float>{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+__device__ __forceinline__ ModeEntry<double> load_mode_shared(const double* t, int idx) {
+  const double2* q = reinterpret_cast<const double2*>(t) + 4 * idx;
+  const double2 a = q[0], b = q[1], c = q[2], d = q[3];
+  return ModeEntry<double>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
+}
+
+// 16-byte asynchronous copy global -> shared (completes at cp_async_wait)
+__device__ __forceinline__ void cp_async16(void* dst_shared, const void* src_global) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src_global) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <typename R>
+__device__ __forceinline__ void mix_entry(cplx<R> (&v)[5], const LPassArgs<R>& a,
+                                          const ModeEntry<R>& m, int ps, int qs, int r);
+
 // linear flow of one Fourier mode (p, q, r in FFT order), including the
 // 1/(NX NY [NZ]) of the forward transforms:
 //   v <- (1 + khat) D v / N = (v + f) / N,  f = e + khat (v + e),  e = (D - I) v.
 template <typename R>
 __device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
                                          int p, int q, int r) {
-  typedef cplx<R> C;
   const int ps = p < a.NX / 2 ? p : p - a.NX;
   const int qs = q < a.NY / 2 ? q : q - a.NY;
   const int aps = ps < 0 ? -ps : ps;
   const int aqs = qs < 0 ? -qs : qs;
   const ModeEntry<R> m = load_mode(a.mt + (size_t)blockIdx.z * a.mt_member, aps * (a.NY / 2 + 1) + aqs);
+  mix_entry<R>(v, a, m, ps, qs, r);
+}
+
+// the flow of the mode (ps, qs) (signed indices) with its table entry m
+template <typename R>
+__device__ __forceinline__ void mix_entry(cplx<R> (&v)[5], const LPassArgs<R>& a,
+                                          const ModeEntry<R>& m, int ps, int qs, int r) {
+  typedef cplx<R> C;
   const C bhat = mkc(ps < 0 ? -m.bx : m.bx, qs < 0 ? m.by : -m.by);
   C kh = mkc(m.khr, m.khi);
   if (a.axis == 2) {
@@ -512,6 +552,28 @@ k_linepass(LPassArgs<R> a) {
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
   const int xcol = blockIdx.x * TILE + col;
   const bool valid = xcol < a.nx;
+  // 2D y-lines with the mix: copy the rows |p| of the mode table that the
+  // tile's columns use (idle columns of a ragged tile use p = 0) into
+  // shared memory behind the exchange buffers; the launch adds Cfg::TAB
+  // bytes of dynamic shared memory for exactly this case
+  constexpr int HN = N / 2 + 1;
+  constexpr int GR = MT_STRIDE * (int)sizeof(R) / 16;          // 16-byte pieces per entry
+  R* smt = reinterpret_cast<R*>(xb + Cfg::NB * TILE * Cfg::LP);
+  const bool stab = (a.mode & LP_MIX) && a.axis == 1;
+  if (stab) {
+    const R* mtm = a.mt + (size_t)blockIdx.z * a.mt_member;
+    for (int k = threadIdx.x; k < TILE * HN * GR; k += Cfg::THREADS) {
+      const int cc = k / (HN * GR);
+      const int rem = k - cc * HN * GR;
+      int p = blockIdx.x * TILE + cc;
+      p = p < a.nx ? p : 0;
+      int ps = p < a.NX / 2 ? p : p - a.NX;
+      ps = ps < 0 ? -ps : ps;
+      cp_async16(reinterpret_cast<char*>(smt) + ((size_t)cc * HN * GR + rem) * 16,
+                 reinterpret_cast<const char*>(mtm) + ((size_t)ps * HN * GR + rem) * 16);
+    }
+    cp_async_commit();
+  }
   C* base = a.field + (size_t)blockIdx.z * 5 * a.ntot + (size_t)blockIdx.y * a.plane_stride +
             (valid ? xcol : 0) + (size_t)i * a.line_stride;
   const size_t step = (size_t)T * a.line_stride;
@@ -526,16 +588,30 @@ k_linepass(LPassArgs<R> a) {
   if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if (a.mode & LP_MIX) {
     const int pm = valid ? xcol : 0;   // idle threads of a ragged tile read mode 0
+    if (stab) {
+      cp_async_wait();
+      __syncthreads();
+      const int ps = pm < a.NX / 2 ? pm : pm - a.NX;
+      const R* tcol = smt + (size_t)col * HN * MT_STRIDE;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int pos = i + T * e;
-      C p5[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
-      if (a.axis == 1)
-        mix_mode<R>(p5, a, pm, pos, 0);
-      else
+      for (int e = 0; e < E; ++e) {
+        const int pos = i + T * e;
+        const int qs = pos < N / 2 ? pos : pos - N;
+        C p5[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
+        const ModeEntry<R> m = load_mode_shared(tcol, qs < 0 ? -qs : qs);
+        mix_entry<R>(p5, a, m, ps, qs, 0);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int pos = i + T * e;
+        C p5[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
         mix_mode<R>(p5, a, pm, blockIdx.y, pos);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
+        for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
+      }
     }
   }
   if (a.mode & LP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
