@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -296,7 +297,13 @@ std::string g_create_err;
 cudaError_t dev_alloc(sgp_ctx* c, void** p, size_t bytes) {
   if (c->alloc.alloc) {
     *p = c->alloc.alloc(bytes, c->device, (void*)c->stream, c->alloc.user);
-    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (!*p) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(*p) % 16 != 0) {   // kernels copy 16-byte pieces
+      c->alloc.free(*p, c->device, (void*)c->stream, c->alloc.user);
+      *p = nullptr;
+      return cudaErrorMisalignedAddress;
+    }
+    return cudaSuccess;
   }
   return cudaMalloc(p, bytes);
 }

@@ -173,8 +173,8 @@ static cudaError_t linepass_n(const LPassArgs<Real>& a, int planes, int members,
   cudaError_t e = linepass_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
-  // the mode-table slice in shared memory for 2D y-lines with the mix
-  const size_t smem = Cfg::SMEM + (((a.mode & LP_MIX) && a.axis == 1) ? Cfg::TAB : 0);
+  // the mode-table entries in shared memory when the pass mixes
+  const size_t smem = Cfg::SMEM + line_table_bytes<Cfg>(a.mode, a.axis);
   k_linepass<Real, N, E, G><<<grid, Cfg::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -458,23 +458,21 @@ struct LCfg {
   // columns x (N/2 + 1) entries), copied to shared memory asynchronously
   // at the start so that the mix does not wait on L2 for every mode
   static constexpr size_t TAB = (size_t)TILE * (N / 2 + 1) * MT_STRIDE * sizeof(R);
-  static_assert(SMEM + TAB <= 227 * 1024, "line pass shared memory");
+  // 3D z-lines: TILE entries and the N z factors
+  static constexpr size_t TABZ = (size_t)TILE * MT_STRIDE * sizeof(R) + (size_t)N * sizeof(cplx<R>);
+  static_assert(SMEM + TAB <= 227 * 1024 && TABZ <= TAB, "line pass shared memory");
 };
+
+// dynamic shared memory added to a line pass for its table copies
+template <typename Cfg>
+inline size_t line_table_bytes(int mode, int axis) {
+  if (!(mode & LP_MIX)) return 0;
+  return axis == 1 ? Cfg::TAB : axis == 2 ? Cfg::TABZ : 0;
+}
 
 template <typename R> struct ModeEntry { R khr, khi, am1r, am1i, cm1, sp, bx, by; };
 
-__device__ __forceinline__ ModeEntry<float> load_mode(const float* mt, int idx) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(mt) + 2 * idx);
-  const float4 b = __ldg(reinterpret_cast<const float4*>(mt) + 2 * idx + 1);
-  return ModeEntry<float>{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-}
-__device__ __forceinline__ ModeEntry<double> load_mode(const double* mt, int idx) {
-  const double2* q = reinterpret_cast<const double2*>(mt) + 4 * idx;
-  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
-  return ModeEntry<double>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
-}
-
-// the same entry from the shared-memory copy of the table slice
+// a mode-table entry from the shared-memory copy of the table
 __device__ __forceinline__ ModeEntry<float> load_mode_shared(const float* t, int idx) {
   const float4 a = reinterpret_cast<const float4*>(t)[2 * idx];
   const float4 b = reinterpret_cast<const float4*>(t)[2 * idx + 1];
@@ -498,35 +496,21 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-template <typename R>
-__device__ __forceinline__ void mix_entry(cplx<R> (&v)[5], const LPassArgs<R>& a,
-                                          const ModeEntry<R>& m, int ps, int qs, int r);
+// the 3D kinetic factor from the (x, y) one and the z one: (1 + kh)(1 + kz) - 1
+template <typename C>
+__device__ __forceinline__ C kinetic_z(C kh, C kz) {
+  return cadd(cadd(kh, kz), cmul(kh, kz));
+}
 
-// linear flow of one Fourier mode (p, q, r in FFT order), including the
+// linear flow of one Fourier mode (signed indices ps, qs) with its table
+// entry m and kinetic factor kh = exp(-i |nu|^2 delta/2) - 1, including the
 // 1/(NX NY [NZ]) of the forward transforms:
 //   v <- (1 + khat) D v / N = (v + f) / N,  f = e + khat (v + e),  e = (D - I) v.
 template <typename R>
-__device__ __forceinline__ void mix_mode(cplx<R> (&v)[5], const LPassArgs<R>& a,
-                                         int p, int q, int r) {
-  const int ps = p < a.NX / 2 ? p : p - a.NX;
-  const int qs = q < a.NY / 2 ? q : q - a.NY;
-  const int aps = ps < 0 ? -ps : ps;
-  const int aqs = qs < 0 ? -qs : qs;
-  const ModeEntry<R> m = load_mode(a.mt + (size_t)blockIdx.z * a.mt_member, aps * (a.NY / 2 + 1) + aqs);
-  mix_entry<R>(v, a, m, ps, qs, r);
-}
-
-// the flow of the mode (ps, qs) (signed indices) with its table entry m
-template <typename R>
 __device__ __forceinline__ void mix_entry(cplx<R> (&v)[5], const LPassArgs<R>& a,
-                                          const ModeEntry<R>& m, int ps, int qs, int r) {
+                                          const ModeEntry<R>& m, int ps, int qs, cplx<R> kh) {
   typedef cplx<R> C;
   const C bhat = mkc(ps < 0 ? -m.bx : m.bx, qs < 0 ? m.by : -m.by);
-  C kh = mkc(m.khr, m.khi);
-  if (a.axis == 2) {
-    const C kz = __ldg(a.kz + r);       // (1 + kh)(1 + kz) - 1
-    kh = cadd(cadd(kh, kz), cmul(kh, kz));
-  }
   C e[5];
   spin2_increment<R>(v, mkc(m.am1r, m.am1i), bhat, m.cm1, m.sp, e);
 #pragma unroll
@@ -552,14 +536,43 @@ k_linepass(LPassArgs<R> a) {
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
   const int xcol = blockIdx.x * TILE + col;
   const bool valid = xcol < a.nx;
-  // 2D y-lines with the mix: copy the rows |p| of the mode table that the
-  // tile's columns use (idle columns of a ragged tile use p = 0) into
-  // shared memory behind the exchange buffers; the launch adds Cfg::TAB
-  // bytes of dynamic shared memory for exactly this case
+  // With the mix, the mode-table entries the tile uses go to shared memory
+  // behind the exchange buffers by asynchronous copies issued here, which
+  // complete while the field loads and the forward transform run (the
+  // launch adds the bytes of line_table_bytes for exactly these cases):
+  //   2D y-lines: the rows |p| of the tile's columns (idle columns of a
+  //     ragged tile use p = 0), TILE x (N/2 + 1) entries;
+  //   3D z-lines: the tile's TILE entries at (|p|, |q|), q = blockIdx.y,
+  //     then the z factors kz[0..N).
   constexpr int HN = N / 2 + 1;
   constexpr int GR = MT_STRIDE * (int)sizeof(R) / 16;          // 16-byte pieces per entry
   R* smt = reinterpret_cast<R*>(xb + Cfg::NB * TILE * Cfg::LP);
   const bool stab = (a.mode & LP_MIX) && a.axis == 1;
+  const bool stabz = (a.mode & LP_MIX) && a.axis == 2;
+  if (stabz) {
+    const R* mtm = a.mt + (size_t)blockIdx.z * a.mt_member;
+    const int qq = blockIdx.y;
+    int aqs = qq < a.NY / 2 ? qq : qq - a.NY;
+    aqs = aqs < 0 ? -aqs : aqs;
+    constexpr int KZ = N * (int)sizeof(C) / 16;
+    for (int k = threadIdx.x; k < TILE * GR + KZ; k += Cfg::THREADS) {
+      if (k < TILE * GR) {
+        const int cc = k / GR, g = k - cc * GR;
+        int p = blockIdx.x * TILE + cc;
+        p = p < a.nx ? p : 0;
+        int ps = p < a.NX / 2 ? p : p - a.NX;
+        ps = ps < 0 ? -ps : ps;
+        cp_async16(reinterpret_cast<char*>(smt) + (size_t)k * 16,
+                   reinterpret_cast<const char*>(mtm) +
+                       ((size_t)(ps * (a.NY / 2 + 1) + aqs) * GR + g) * 16);
+      } else {
+        const int kk = k - TILE * GR;
+        cp_async16(reinterpret_cast<char*>(smt) + (size_t)k * 16,
+                   reinterpret_cast<const char*>(a.kz) + (size_t)kk * 16);
+      }
+    }
+    cp_async_commit();
+  }
   if (stab) {
     const R* mtm = a.mt + (size_t)blockIdx.z * a.mt_member;
     for (int k = threadIdx.x; k < TILE * HN * GR; k += Cfg::THREADS) {
@@ -599,16 +612,24 @@ k_linepass(LPassArgs<R> a) {
         const int qs = pos < N / 2 ? pos : pos - N;
         C p5[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
         const ModeEntry<R> m = load_mode_shared(tcol, qs < 0 ? -qs : qs);
-        mix_entry<R>(p5, a, m, ps, qs, 0);
+        mix_entry<R>(p5, a, m, ps, qs, mkc(m.khr, m.khi));
 #pragma unroll
         for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
       }
-    } else {
+    } else if (stabz) {
+      cp_async_wait();
+      __syncthreads();
+      const int ps = pm < a.NX / 2 ? pm : pm - a.NX;
+      const int qq = blockIdx.y;
+      const int qs = qq < a.NY / 2 ? qq : qq - a.NY;
+      const ModeEntry<R> m = load_mode_shared(smt, col);
+      const C kh = mkc(m.khr, m.khi);
+      const C* skz = reinterpret_cast<const C*>(smt + TILE * MT_STRIDE);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int pos = i + T * e;
         C p5[5] = {v[0][e], v[1][e], v[2][e], v[3][e], v[4][e]};
-        mix_mode<R>(p5, a, pm, blockIdx.y, pos);
+        mix_entry<R>(p5, a, m, ps, qs, kinetic_z(kh, skz[pos]));
 #pragma unroll
         for (int c = 0; c < 5; ++c) v[c][e] = p5[c];
       }
