@@ -187,8 +187,14 @@ __device__ __forceinline__ void sincos_small(float a, float* s, float* c) {
   }
 }
 __device__ __forceinline__ void sincos_small(double a, double* s, double* c) { sincos(a, s, c); }
-// 1/a rounded to nearest (FP32) or IEEE division (FP64)
-__device__ __forceinline__ float rcp_r(float a) { return __frcp_rn(a); }
+// 1/a: IEEE division in FP64
+// 1/a (FP32): the hardware estimate refined by one Newton-Raphson step,
+// r + r (1 - a r), within about an ulp (the arguments here lie in (0, 2]).
+__device__ __forceinline__ float rcp_r(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return fmaf(r, fmaf(-a, r, 1.0f), r);
+}
 __device__ __forceinline__ double rcp_r(double a) { return 1.0 / a; }
 
 __device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
@@ -363,17 +369,31 @@ k_xpass(XPassArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
   C* xb = reinterpret_cast<C*>(tw + N);
-  __shared__ R s_rot[2];
+  // rotation cos/sin and the member's parameters in R, formed once per CTA
+  // (FP64 work runs at a small fraction of the FP32 rate on this part)
+  __shared__ R s_prm[8];
+  __shared__ R s_yz[Cfg::ROWS][2];    // y and z of the CTA's rows
   const int g = threadIdx.x / T;
   const int i = threadIdx.x - g * T;
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
-  const MemberPrm& P = a.mp[blockIdx.y];
   if ((a.mode & XP_NL) && threadIdx.x == 0) {
+    const MemberPrm& P = a.mp[blockIdx.y];
     const double t = *a.t_base + a.t_off;
     double sn, cs;
     sincos(P.omega * t, &sn, &cs);
-    s_rot[0] = (R)cs;
-    s_rot[1] = (R)sn;
+    s_prm[0] = (R)cs;
+    s_prm[1] = (R)sn;
+    s_prm[2] = (R)(P.c0 + P.c2 / 5.0);
+    s_prm[3] = (R)P.c1;
+    s_prm[4] = (R)P.c2;
+    s_prm[5] = (R)P.gx2h;
+    s_prm[6] = (R)P.gy2h;
+    s_prm[7] = (R)P.gz2h;
+  }
+  if ((a.mode & XP_NL) && threadIdx.x < Cfg::ROWS) {
+    const int rr = blockIdx.x * Cfg::ROWS + threadIdx.x;
+    s_yz[threadIdx.x][0] = a.y0 + (R)(rr % a.ny) * a.hy;
+    s_yz[threadIdx.x][1] = a.z0 + (R)(rr / a.ny) * a.hz;
   }
   const int row = blockIdx.x * Cfg::ROWS + g;
   const bool valid = row < a.rows;
@@ -389,23 +409,21 @@ k_xpass(XPassArgs<R> a) {
   if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if (a.mode & XP_NL) {
     C* stg = xb;                      // [ROWS][5][N], aliases the exchange buffers
-    __syncthreads();                  // exchange buffers free, s_rot visible
+    __syncthreads();                  // exchange buffers free, s_prm visible
 #pragma unroll
     for (int c = 0; c < 5; ++c)
 #pragma unroll
       for (int e = 0; e < E; ++e) stg[(g * 5 + c) * N + i + T * e] = v[c][e];
     __syncthreads();
-    const R co = s_rot[0], si = s_rot[1];
-    const R c0p = (R)(P.c0 + P.c2 / 5.0), c1 = (R)P.c1, c2 = (R)P.c2;
-    const R gx2h = (R)P.gx2h, gy2h = (R)P.gy2h, gz2h = (R)P.gz2h;
+    const R co = s_prm[0], si = s_prm[1];
+    const R c0p = s_prm[2], c1 = s_prm[3], c2 = s_prm[4];
+    const R gx2h = s_prm[5], gy2h = s_prm[6], gz2h = s_prm[7];
 #pragma unroll 1
     for (int pnt = threadIdx.x; pnt < Cfg::ROWS * N; pnt += Cfg::THREADS) {
       const int gg = pnt / N, j = pnt - gg * N;
-      const int rr = blockIdx.x * Cfg::ROWS + gg;
-      const int ky = rr % a.ny, kz = rr / a.ny;
       const R x = a.x0 + (R)j * a.hx;
-      const R y = a.y0 + (R)ky * a.hy;
-      const R z = a.z0 + (R)kz * a.hz;
+      const R y = s_yz[gg][0];
+      const R z = s_yz[gg][1];
       const R xr = co * x + si * y;
       const R yr = co * y - si * x;
       const R V = gx2h * xr * xr + gy2h * yr * yr + gz2h * z * z;
