@@ -147,8 +147,8 @@ sgp_status sgp_set_params_batch(sgp_ctx* ctx, const sgp_params* p, int count);
  * and the autotuner's scratch.  Each context keeps the pair it was created
  * with until sgp_destroy; frees synchronise the context stream first.
  * Returned blocks must be 16-byte aligned (the kernels move 16-byte
- * pieces); a misaligned block is handed back to free_fn at once and the
- * call fails with SGP_ECUDA.
+ * pieces); a misaligned block is handed back to free_fn at once and counts
+ * as a failed allocation.
  * alloc = free_fn = NULL restores cudaMalloc/cudaFree.  Process-wide, not
  * thread-safe against concurrent sgp_create_grid.  An allocation failure
  * makes the calling entry point return SGP_ENOMEM or SGP_ECUDA.  Errors:

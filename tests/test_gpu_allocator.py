@@ -90,3 +90,28 @@ def test_failing_allocator_reports_enomem():
         sgp.use_torch_allocator(False)
     c = sgp.Context((64, 64), 8.0, prec="f32")     # the default is back
     c.close()
+
+
+def test_misaligned_allocator_block_is_refused_and_freed():
+    """A block that is not 16-byte aligned is handed back at once and the
+    creation fails as for a failed allocation; no kernel touches it."""
+    held, freed = {}, []
+
+    def _alloc(size, device, stream, user):
+        t = torch.empty(size + 64, dtype=torch.uint8, device="cuda:%d" % device)
+        p = t.data_ptr() + 8
+        held[p] = t
+        return p
+
+    def _free(p, device, stream, user):
+        freed.append(p)
+        held.pop(p, None)
+
+    keep = (sgp.ALLOC_FN(_alloc), sgp.FREE_FN(_free))
+    try:
+        assert sgp.lib().sgp_set_allocator(keep[0], keep[1], None) == 0
+        with pytest.raises(sgp.SgpError, match="ENOMEM.*misaligned"):
+            sgp.Context((64, 64), 8.0, prec="f32")
+        assert freed and not held
+    finally:
+        sgp.use_torch_allocator(False)
