@@ -205,6 +205,24 @@ sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
  * before sgp_set_state; SGP_ECUDA if a launch fails. */
 sgp_status sgp_step(sgp_ctx* ctx, long long nsteps, double dt, int scheme);
 
+/* Host-to-host propagation with the copies overlapped: the same result, bit
+ * for bit, as sgp_set_state(ctx, host_in, 0, t0); sgp_step(ctx, nsteps,
+ * dt, scheme); sgp_get_state(ctx, host_out, 0), but the batch is split into
+ * `chunks` groups of consecutive members and the copies of the other groups
+ * (to the device on one copy stream, back on another) run while a group is
+ * propagated on the context stream (members are independent, Sec. 3).
+ * host_in, host_out: [batch][5][nz][ny][nx] complex in the context's
+ * precision, owned by the caller, may be the same buffer; page-locked
+ * memory is needed for the overlap (pageable memory gives the same result
+ * without it).  Returns when host_out holds the state at t0 + nsteps*dt.
+ * Each group runs its steps with direct launches (no graph replay); the
+ * health check does not run in this call.  Errors: SGP_EINVAL for NULL
+ * buffers, chunks outside [1, batch], nsteps < 0, dt <= 0 or non-finite,
+ * non-finite t0, an unknown scheme; SGP_ECUDA for a failed copy or launch
+ * (the host buffers are no longer in use when the call returns). */
+sgp_status sgp_step_host(sgp_ctx* ctx, const void* host_in, double t0, void* host_out,
+                         long long nsteps, double dt, int scheme, int chunks);
+
 /* Health check of sgp_step (off by default).  With every > 0, sgp_step
  * runs in chunks of at most `every` steps and after each chunk sums every
  * member's mass h^d sum |phi|^2 in FP64 on the device (Sec. 2: the scheme

@@ -286,6 +286,11 @@ struct sgp_ctx {
   bool health_ref = false;          // m0 holds the mass at the last set_state
   std::vector<double> m0;
   double* mass_dev = nullptr;       // [batch] + partials
+  // member window of the passes: members [win0, win0 + wcnt) (wcnt = 0:
+  // the whole batch); set only inside sgp_step_host
+  int win0 = 0, wcnt = 0;
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;   // copy streams of sgp_step_host
+  std::vector<cudaEvent_t> pipe_ev;                 // its ordering events
   Allocator alloc;                  // taken from g_allocator at creation
   std::string err;
 };
@@ -470,6 +475,12 @@ sgp_status get_tables(sgp_ctx* c, double delta, const LinTables** out) {
 // ----------------------------------------------------------------------------
 // passes
 // ----------------------------------------------------------------------------
+// members the passes work on and the field of the first of them
+int window_members(const sgp_ctx* c) { return c->wcnt ? c->wcnt : c->batch; }
+void* window_field(sgp_ctx* c) {
+  return (char*)c->field + (size_t)c->win0 * 5 * c->ntot * c->elem;
+}
+
 template <typename R>
 sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
   XPassArgs<R> a{};
@@ -486,18 +497,18 @@ sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_o
   a.z0 = c->dim == 3 ? (R)-c->L[2] : (R)0;
   a.hz = c->dim == 3 ? (R)c->h[2] : (R)0;
   a.delta = (R)delta;
-  a.mp = c->mp_dev;
+  a.mp = c->mp_dev + c->win0;
   a.t_base = c->t_dev;
   a.t_off = t_off;
   c->launches++;
   ProfScope ps(c, PK_X);
-  SGP_CUDA(c, launch_xpass<R>(c->n[0], c->var[0], a, c->batch, c->stream));
+  SGP_CUDA(c, launch_xpass<R>(c->n[0], c->var[0], a, window_members(c), c->stream));
   return SGP_OK;
 }
 
 template <typename R>
 sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
-  return x_pass_on<R>(c, c->field, mode, delta, t_off);
+  return x_pass_on<R>(c, window_field(c), mode, delta, t_off);
 }
 
 // axis 1: lines along y (planes = z slices); axis 2: lines along z (planes = y rows)
@@ -524,8 +535,8 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
   a.NX = c->n[0];
   a.NY = c->n[1];
   if (t) {
-    a.mt = (const R*)t->mt;
     a.mt_member = c->shared_lin ? 0 : (long long)(c->n[0] / 2 + 1) * (c->n[1] / 2 + 1) * MT_STRIDE;
+    a.mt = (const R*)t->mt + (size_t)c->win0 * a.mt_member;
     a.kz = (const cplx<R>*)t->kz;
   }
   {
@@ -535,13 +546,13 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
   }
   c->launches++;
   ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
-  SGP_CUDA(c, launch_linepass<R>(c->n[axis], c->var[axis], a, planes, c->batch, c->stream));
+  SGP_CUDA(c, launch_linepass<R>(c->n[axis], c->var[axis], a, planes, window_members(c), c->stream));
   return SGP_OK;
 }
 
 template <typename R>
 sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
-  return line_pass_on<R>(c, c->field, axis, mode, t);
+  return line_pass_on<R>(c, window_field(c), axis, mode, t);
 }
 
 // Linear flow over delta between x-passes.  Entry: x-spectral (the x-pass
@@ -562,7 +573,7 @@ sgp_status linear_middle_on(sgp_ctx* c, void* f, double delta) {
 
 template <typename R>
 sgp_status linear_middle(sgp_ctx* c, double delta) {
-  return linear_middle_on<R>(c, c->field, delta);
+  return linear_middle_on<R>(c, window_field(c), delta);
 }
 
 // substep pattern of one step, Sec. 3.3
@@ -716,7 +727,7 @@ sgp_status run_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
   }
   SGP_CUDA(c, cudaGetLastError());
   long long done = 0;
-  if (c->use_graphs && !c->profiling && nsteps >= 2 * kGraphChunk) {
+  if (c->use_graphs && !c->profiling && c->wcnt == 0 && nsteps >= 2 * kGraphChunk) {
     cudaGraphExec_t exec = nullptr;
     SGP_TRY(get_graph<R>(c, kGraphChunk, dt, scheme, &exec));
     const long long reps = nsteps / kGraphChunk;
@@ -742,6 +753,78 @@ sgp_status substep(sgp_ctx* c, int kind, double delta) {
     SGP_TRY(x_pass<R>(c, XP_INV, 0.0, 0.0));
     c->t += delta;
   }
+  return SGP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// host-to-host propagation with the copies overlapped (sgp_step_host)
+// ----------------------------------------------------------------------------
+// The batch is split into `chunks` member groups.  All copies to the device
+// are issued on cs_in, each group's steps on the context stream after its
+// copy has landed (the passes restricted to the group by the member
+// window), and each group's copy back on cs_out after its steps: the copy
+// engines move group k+1 in and group k-1 out while group k is propagated.
+template <typename R>
+sgp_status step_host_impl(sgp_ctx* c, const void* hin, double t0, void* hout, long long nsteps,
+                          double dt, int scheme, int chunks) {
+  if (!c->cs_in) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking));
+  if (!c->cs_out) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking));
+  const size_t nev = 2 * (size_t)chunks + 2;
+  while (c->pipe_ev.size() < nev) {
+    cudaEvent_t e = nullptr;
+    SGP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->pipe_ev.push_back(e);
+  }
+  cudaEvent_t* ev = c->pipe_ev.data();   // [0] start, [1] end, then in[k], done[k]
+  const size_t mb = (size_t)5 * c->ntot * c->elem;
+  std::vector<int> m0(chunks + 1);
+  for (int k = 0; k <= chunks; ++k) m0[k] = (int)((long long)c->batch * k / chunks);
+  // earlier work of the context stream on the field comes first
+  SGP_CUDA(c, cudaEventRecord(ev[0], c->stream));
+  SGP_CUDA(c, cudaStreamWaitEvent(c->cs_in, ev[0], 0));
+  SGP_CUDA(c, cudaStreamWaitEvent(c->cs_out, ev[0], 0));
+  for (int k = 0; k < chunks; ++k) {
+    const size_t off = (size_t)m0[k] * mb, bytes = (size_t)(m0[k + 1] - m0[k]) * mb;
+    SGP_CUDA(c, cudaMemcpyAsync((char*)c->field + off, (const char*)hin + off, bytes,
+                                cudaMemcpyHostToDevice, c->cs_in));
+    SGP_CUDA(c, cudaEventRecord(ev[2 + k], c->cs_in));
+  }
+  c->adj.valid = false;
+  c->health_ref = false;
+  c->have_state = true;
+  sgp_status st = SGP_OK;
+  for (int k = 0; k < chunks && st == SGP_OK; ++k) {
+    const size_t off = (size_t)m0[k] * mb, bytes = (size_t)(m0[k + 1] - m0[k]) * mb;
+    cudaError_t e = cudaStreamWaitEvent(c->stream, ev[2 + k], 0);
+    if (e != cudaSuccess) {
+      st = fail(c, SGP_ECUDA, "stream wait: %s", cudaGetErrorString(e));
+      break;
+    }
+    c->win0 = m0[k];
+    c->wcnt = m0[k + 1] - m0[k];
+    c->t = t0;
+    if (nsteps > 0) st = run_steps<R>(c, nsteps, dt, scheme);
+    c->win0 = 0;
+    c->wcnt = 0;
+    if (st != SGP_OK) break;
+    e = cudaEventRecord(ev[2 + chunks + k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs_out, ev[2 + chunks + k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char*)hout + off, (const char*)c->field + off, bytes,
+                          cudaMemcpyDeviceToHost, c->cs_out);
+    if (e != cudaSuccess) st = fail(c, SGP_ECUDA, "copy back: %s", cudaGetErrorString(e));
+  }
+  c->t = t0 + (double)nsteps * dt;
+  // later work of the context stream comes after the copies back; the host
+  // buffers are done with when this returns, also after an error
+  cudaError_t e = cudaEventRecord(ev[1], c->cs_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, ev[1], 0);
+  const cudaError_t e1 = cudaStreamSynchronize(c->cs_in);
+  const cudaError_t e2 = cudaStreamSynchronize(c->cs_out);
+  const cudaError_t e3 = cudaStreamSynchronize(c->stream);
+  if (st != SGP_OK) return st;
+  for (cudaError_t x : {e, e1, e2, e3})
+    if (x != cudaSuccess) return fail(c, SGP_ECUDA, "sgp_step_host: %s", cudaGetErrorString(x));
   return SGP_OK;
 }
 
@@ -1591,6 +1674,21 @@ sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
                             : run_steps<double>(c, nsteps, dt, scheme);
 }
 
+sgp_status sgp_step_host(sgp_ctx* c, const void* host_in, double t0, void* host_out,
+                         long long nsteps, double dt, int scheme, int chunks) {
+  if (!c) return SGP_EINVAL;
+  if (!host_in || !host_out) return fail(c, SGP_EINVAL, "NULL host buffer");
+  if (chunks < 1 || chunks > c->batch)
+    return fail(c, SGP_EINVAL, "chunks %d not in [1, batch = %d]", chunks, c->batch);
+  if (nsteps < 0) return fail(c, SGP_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SGP_EINVAL, "dt must be positive and finite");
+  if (!std::isfinite(t0)) return fail(c, SGP_EINVAL, "non-finite t0");
+  if (!valid_scheme(scheme)) return fail(c, SGP_EINVAL, "unknown scheme %d", scheme);
+  DeviceGuard guard(c->device);
+  return c->prec == SGP_F32 ? step_host_impl<float>(c, host_in, t0, host_out, nsteps, dt, scheme, chunks)
+                            : step_host_impl<double>(c, host_in, t0, host_out, nsteps, dt, scheme, chunks);
+}
+
 sgp_status sgp_set_health_check(sgp_ctx* c, long long every, double drift_tol) {
   if (!c) return SGP_EINVAL;
   if (every < 0) return fail(c, SGP_EINVAL, "every < 0");
@@ -1761,6 +1859,9 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   dev_free(c, c->mass_dev);
   recycle_events(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->pipe_ev) cudaEventDestroy(e);
+  if (c->cs_in) cudaStreamDestroy(c->cs_in);
+  if (c->cs_out) cudaStreamDestroy(c->cs_out);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SGP_OK;

@@ -98,6 +98,7 @@ def lib():
         "sgp_get_time": (I, [P, ctypes.POINTER(ctypes.c_double)]),
         "sgp_get_state_lab": (I, [P, P, I]),
         "sgp_step": (I, [P, LL, D, I]),
+        "sgp_step_host": (I, [P, P, D, P, LL, D, I, I]),
         "sgp_substep": (I, [P, I, D]),
         "sgp_observables": (I, [P, ctypes.POINTER(Obs)]),
         "sgp_synchronize": (I, [P]),
@@ -248,6 +249,18 @@ def get_time(ctx):
 def step(ctx, nsteps, dt, scheme="ts2"):
     s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
     _check(lib().sgp_step(ctx, int(nsteps), float(dt), s), ctx)
+
+
+def step_host(ctx, src, t0, dst, nsteps, dt, scheme, chunks, dtype):
+    """sgp_step_host: host buffers in and out, copies overlapped with the steps."""
+    pi, di, _ki = _ptr(src, dtype)
+    po, do, _ko = _ptr(dst, dtype)
+    if di or do:
+        raise ValueError("sgp_step_host takes host buffers")
+    s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+    _check(lib().sgp_step_host(ctx, ctypes.c_void_p(pi), float(t0), ctypes.c_void_p(po),
+                               int(nsteps), float(dt), s, int(chunks)), ctx)
+    return dst
 
 
 SGP_TUNE_FORCE = 1
@@ -411,6 +424,13 @@ class Context:
 
     def step(self, nsteps, dt, scheme="ts2"):
         step(self.handle, nsteps, dt, scheme)
+
+    def step_host(self, src, t0, nsteps, dt, scheme="ts2", chunks=1, out=None):
+        """State from host memory, nsteps steps, state back to host memory
+        (sgp_step_host); `out` defaults to a new array."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        return step_host(self.handle, src, t0, out, nsteps, dt, scheme, chunks, self.dtype)
 
     def substep(self, kind, delta):
         substep(self.handle, kind, delta)

@@ -1,0 +1,94 @@
+"""sgp_step_host (host buffers in and out, the copies of the other member
+groups overlapped with the steps of one) against the same run through
+sgp_set_state / sgp_step / sgp_get_state: bit-identical results for every
+split of the batch (uneven groups included), per-member parameters (the
+member window into the per-member tables), 2D and 3D, both precisions,
+in-place buffers; the time, the state left on the device, and the errors.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import sgp_oracle as O
+from paper_2603_25282_gb300 import inputs, sgp
+
+pytestmark = pytest.mark.gpu
+
+
+def _plist(batch):
+    rng = np.random.default_rng(7)
+    return [dict(omega=float(rng.uniform(0.1, 0.9)), gamma=float(rng.uniform(0.5, 1.5)),
+                 c0=float(rng.uniform(50, 200)), c1=float(rng.uniform(-3, 3)),
+                 c2=float(rng.uniform(0, 5)), gx=1.0, gy=1.2, gz=1.5) for _ in range(batch)]
+
+
+def _states(n, L, batch, dtype):
+    return np.stack([inputs.gaussian_random_phase(n, L, seed=60 + m, amp=0.4)
+                     for m in range(batch)]).astype(dtype)
+
+
+def _pinned(a):
+    return torch.from_numpy(a).pin_memory()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n,L,scheme,nsteps", [((64, 48), (8.0, 6.0), "ts4", 7),
+                                               ((32, 32, 16), (5.0, 5.0, 4.0), "ts2", 5)])
+def test_step_host_equals_set_step_get(prec, n, L, scheme, nsteps):
+    batch = 5
+    dtype = np.complex64 if prec == "f32" else np.complex128
+    psi = _states(n, L, batch, dtype)
+    c = sgp.Context(n, L, batch=batch, prec=prec)
+    c.set_params_batch(_plist(batch))
+    c.set_state(psi.copy(), 0.3)
+    c.step(nsteps, 1e-3, scheme)
+    ref = c.get_state()
+    t_ref = c.t
+    for chunks in (1, 2, 3, 5):
+        out = torch.empty(psi.shape, dtype=torch.complex64 if prec == "f32" else torch.complex128).pin_memory()
+        c.step_host(_pinned(psi), 0.3, nsteps, 1e-3, scheme, chunks=chunks, out=out)
+        assert np.array_equal(out.numpy(), ref), chunks
+        assert c.t == t_ref
+        assert np.array_equal(c.get_state(), ref)      # the state stays on the device
+    c.close()
+
+
+def test_step_host_in_place_pageable_and_continuation():
+    n, L, batch = (48, 48), 6.0, 4
+    psi = _states(n, L, batch, np.complex64)
+    prm = _plist(batch)
+    a = sgp.Context(n, L, batch=batch, prec="f32")
+    a.set_params_batch(prm)
+    a.set_state(psi.copy(), 0.0)
+    a.step(20, 1e-3, "ts4")
+    ref = a.get_state()
+    b = sgp.Context(n, L, batch=batch, prec="f32")
+    b.set_params_batch(prm)
+    buf = psi.copy()                                   # pageable, in and out the same
+    b.step_host(buf, 0.0, 10, 1e-3, "ts4", chunks=3, out=buf)
+    b.step(10, 1e-3, "ts4")                            # continues from the device state
+    # 10 + 10 steps in two calls: the step sequence restarts at the call
+    # boundary, so the comparison is at the FP32 level
+    out = b.get_state()
+    for m in range(batch):
+        assert O.rel_l2(out[m].astype(np.complex128), ref[m].astype(np.complex128)) < 2e-6
+    assert abs(b.t - 0.02) < 1e-15
+    a.close()
+    b.close()
+
+
+def test_step_host_errors():
+    c = sgp.Context((32, 32), 4.0, batch=2, prec="f32")
+    psi = _states((32, 32), 4.0, 2, np.complex64)
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        c.step_host(psi, 0.0, 1, 1e-3, chunks=0)
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        c.step_host(psi, 0.0, 1, 1e-3, chunks=3)
+    with pytest.raises(sgp.SgpError, match="EINVAL"):
+        c.step_host(psi, float("nan"), 1, 1e-3, chunks=1)
+    with pytest.raises(ValueError):
+        c.step_host(torch.from_numpy(psi).cuda(), 0.0, 1, 1e-3, chunks=1)
+    out = c.step_host(psi, 0.0, 0, 1e-3, chunks=2)     # zero steps: a round trip
+    assert np.array_equal(out, psi)
+    c.close()
