@@ -290,6 +290,8 @@ struct sgp_ctx {
   // the whole batch); set only inside sgp_step_host
   int win0 = 0, wcnt = 0;
   cudaStream_t cs_in = nullptr, cs_out = nullptr;   // copy streams of sgp_step_host
+  cudaStream_t cs_alt = nullptr;                    // its second compute stream
+  double* t_dev_alt = nullptr;                      // and that stream's device time
   std::vector<cudaEvent_t> pipe_ev;                 // its ordering events
   Allocator alloc;                  // taken from g_allocator at creation
   std::string err;
@@ -661,11 +663,15 @@ sgp_status emit_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
 // included (before a capture).
 template <typename R>
 sgp_status ensure_tables(sgp_ctx* c, double dt, int scheme) {
-  for (auto& st : merged_substeps(scheme, 3, dt))
-    if (st.kind == 'L') {
-      const LinTables* t = nullptr;
-      SGP_TRY(get_tables<R>(c, st.delta, &t));
-    }
+  // two passes: a full cache is emptied when a new table is made, which can
+  // drop a table the first pass made; the second makes it again (a scheme
+  // needs at most three sizes, so it evicts nothing)
+  for (int pass = 0; pass < 2; ++pass)
+    for (auto& st : merged_substeps(scheme, 3, dt))
+      if (st.kind == 'L') {
+        const LinTables* t = nullptr;
+        SGP_TRY(get_tables<R>(c, st.delta, &t));
+      }
   return SGP_OK;
 }
 
@@ -760,15 +766,21 @@ sgp_status substep(sgp_ctx* c, int kind, double delta) {
 // host-to-host propagation with the copies overlapped (sgp_step_host)
 // ----------------------------------------------------------------------------
 // The batch is split into `chunks` member groups.  All copies to the device
-// are issued on cs_in, each group's steps on the context stream after its
-// copy has landed (the passes restricted to the group by the member
-// window), and each group's copy back on cs_out after its steps: the copy
-// engines move group k+1 in and group k-1 out while group k is propagated.
+// are issued on cs_in; each group's steps run after its copy has landed
+// (the passes restricted to the group by the member window), alternately
+// on the context stream and on cs_alt with its own device time, so that
+// the last passes of one group overlap the first of the next; each group's
+// copy back runs on cs_out after its steps.  The copy engines move group
+// k+1 in and group k-1 out while group k is propagated.
 template <typename R>
 sgp_status step_host_impl(sgp_ctx* c, const void* hin, double t0, void* hout, long long nsteps,
                           double dt, int scheme, int chunks) {
   if (!c->cs_in) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking));
   if (!c->cs_out) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking));
+  if (!c->cs_alt) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_alt, cudaStreamNonBlocking));
+  if (!c->t_dev_alt) SGP_CUDA(c, dev_alloc(c, (void**)&c->t_dev_alt, sizeof(double)));
+  // the linear-flow tables of the run exist before the streams fork
+  if (nsteps > 0) SGP_TRY(ensure_tables<R>(c, dt, scheme));
   const size_t nev = 2 * (size_t)chunks + 2;
   while (c->pipe_ev.size() < nev) {
     cudaEvent_t e = nullptr;
@@ -783,6 +795,7 @@ sgp_status step_host_impl(sgp_ctx* c, const void* hin, double t0, void* hout, lo
   SGP_CUDA(c, cudaEventRecord(ev[0], c->stream));
   SGP_CUDA(c, cudaStreamWaitEvent(c->cs_in, ev[0], 0));
   SGP_CUDA(c, cudaStreamWaitEvent(c->cs_out, ev[0], 0));
+  SGP_CUDA(c, cudaStreamWaitEvent(c->cs_alt, ev[0], 0));
   for (int k = 0; k < chunks; ++k) {
     const size_t off = (size_t)m0[k] * mb, bytes = (size_t)(m0[k + 1] - m0[k]) * mb;
     SGP_CUDA(c, cudaMemcpyAsync((char*)c->field + off, (const char*)hin + off, bytes,
@@ -795,19 +808,28 @@ sgp_status step_host_impl(sgp_ctx* c, const void* hin, double t0, void* hout, lo
   sgp_status st = SGP_OK;
   for (int k = 0; k < chunks && st == SGP_OK; ++k) {
     const size_t off = (size_t)m0[k] * mb, bytes = (size_t)(m0[k + 1] - m0[k]) * mb;
-    cudaError_t e = cudaStreamWaitEvent(c->stream, ev[2 + k], 0);
-    if (e != cudaSuccess) {
-      st = fail(c, SGP_ECUDA, "stream wait: %s", cudaGetErrorString(e));
-      break;
+    // odd groups on the second compute stream with its own device time
+    const bool alt = (k & 1) != 0;
+    if (alt) {
+      std::swap(c->stream, c->cs_alt);
+      std::swap(c->t_dev, c->t_dev_alt);
     }
+    cudaError_t e = cudaStreamWaitEvent(c->stream, ev[2 + k], 0);
     c->win0 = m0[k];
     c->wcnt = m0[k + 1] - m0[k];
     c->t = t0;
-    if (nsteps > 0) st = run_steps<R>(c, nsteps, dt, scheme);
+    if (e != cudaSuccess)
+      st = fail(c, SGP_ECUDA, "stream wait: %s", cudaGetErrorString(e));
+    else if (nsteps > 0)
+      st = run_steps<R>(c, nsteps, dt, scheme);
     c->win0 = 0;
     c->wcnt = 0;
+    if (st == SGP_OK) e = cudaEventRecord(ev[2 + chunks + k], c->stream);
+    if (alt) {
+      std::swap(c->stream, c->cs_alt);
+      std::swap(c->t_dev, c->t_dev_alt);
+    }
     if (st != SGP_OK) break;
-    e = cudaEventRecord(ev[2 + chunks + k], c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs_out, ev[2 + chunks + k], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync((char*)hout + off, (const char*)c->field + off, bytes,
@@ -822,8 +844,9 @@ sgp_status step_host_impl(sgp_ctx* c, const void* hin, double t0, void* hout, lo
   const cudaError_t e1 = cudaStreamSynchronize(c->cs_in);
   const cudaError_t e2 = cudaStreamSynchronize(c->cs_out);
   const cudaError_t e3 = cudaStreamSynchronize(c->stream);
+  const cudaError_t e4 = cudaStreamSynchronize(c->cs_alt);
   if (st != SGP_OK) return st;
-  for (cudaError_t x : {e, e1, e2, e3})
+  for (cudaError_t x : {e, e1, e2, e3, e4})
     if (x != cudaSuccess) return fail(c, SGP_ECUDA, "sgp_step_host: %s", cudaGetErrorString(x));
   return SGP_OK;
 }
@@ -1862,6 +1885,8 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   for (cudaEvent_t e : c->pipe_ev) cudaEventDestroy(e);
   if (c->cs_in) cudaStreamDestroy(c->cs_in);
   if (c->cs_out) cudaStreamDestroy(c->cs_out);
+  if (c->cs_alt) cudaStreamDestroy(c->cs_alt);
+  dev_free(c, c->t_dev_alt);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SGP_OK;
