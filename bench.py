@@ -671,19 +671,15 @@ def run_ens(args, rank, world, local_rank):
                                                           amp=0.01).astype(cdt)).pin_memory()
             for m in members]
     outs = [torch.empty_like(h).pin_memory() for h in host]
-    e2e_n = 2
+    e2e_n = 4
     tcur = 0.0                      # the ensemble clock, accumulated as the library does
     tcur += args.warmup * cfg["dt"]
     tcur += args.steps * cfg["dt"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_n):
-        for i, h in enumerate(host):
-            ens.set_member_state(i, h, tcur)
-        ens.step(1, cfg["dt"], cfg["scheme"])
+    for _ in range(e2e_n):            # one sgp_ensemble_step_host call per step
+        ens.step_host(host, tcur, 1, cfg["dt"], cfg["scheme"], outs=outs)
         tcur += 1 * cfg["dt"]
-        for i, o in enumerate(outs):
-            ens.get_member_state(i, o)
     ens.synchronize()
     e2e_s = rep.max_over_ranks(time.perf_counter() - t0)
     if rank == 0:

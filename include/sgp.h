@@ -341,6 +341,19 @@ sgp_status sgp_ensemble_get_member_state(sgp_ens* ens, int member, void* dst,
                                          int dst_on_device);
 /* Advance every member by nsteps steps (asynchronous). */
 sgp_status sgp_ensemble_step(sgp_ens* ens, long long nsteps, double dt, int scheme);
+/* Host round trip of the whole ensemble in one call: every member's state
+ * from host_in[m] at time t0, nsteps steps, every member's state to
+ * host_out[m] (arrays of count pointers; member m's buffer holds its
+ * 5*nz*ny*nx elements; host_in[m] may equal host_out[m]).  The same result
+ * as count sgp_ensemble_set_member_state calls, sgp_ensemble_step and count
+ * sgp_ensemble_get_member_state calls, with the copies issued
+ * asynchronously in stream order and a single synchronisation at the end
+ * (page-locked buffers let the copies run at full speed).  Returns when
+ * every host_out[m] holds its result.  Errors: SGP_EINVAL for NULL arrays
+ * or buffers, non-finite t0, nsteps < 0, dt <= 0, an unknown scheme;
+ * SGP_ECUDA for a failed copy or launch. */
+sgp_status sgp_ensemble_step_host(sgp_ens* ens, const void* const* host_in, double t0,
+                                  void* const* host_out, long long nsteps, double dt, int scheme);
 /* Observables of every member into out[0..count-1] (synchronises). */
 sgp_status sgp_ensemble_observables(sgp_ens* ens, sgp_obs* out);
 /* sgp_autotune for every grid group of the ensemble (flags as there);

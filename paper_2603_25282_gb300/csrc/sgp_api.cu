@@ -2168,6 +2168,53 @@ sgp_status sgp_ensemble_get_member_state(sgp_ens* e, int member, void* dst, int 
   return SGP_OK;
 }
 
+sgp_status sgp_ensemble_step_host(sgp_ens* e, const void* const* host_in, double t0,
+                                  void* const* host_out, long long nsteps, double dt, int scheme) {
+  if (!e) return SGP_EINVAL;
+  if (!host_in || !host_out) return efail(e, SGP_EINVAL, "NULL pointer array");
+  for (int m = 0; m < e->count; ++m)
+    if (!host_in[m] || !host_out[m]) return efail(e, SGP_EINVAL, "NULL host buffer (member %d)", m);
+  if (!std::isfinite(t0)) return efail(e, SGP_EINVAL, "non-finite t0");
+  if (nsteps < 0) return efail(e, SGP_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return efail(e, SGP_EINVAL, "dt must be positive and finite");
+  if (!valid_scheme(scheme)) return efail(e, SGP_EINVAL, "unknown scheme %d", scheme);
+  DeviceGuard guard(e->device);
+  // every copy in, the steps and every copy out in the order of the
+  // ensemble stream, one synchronisation at the end
+  cudaError_t ce = cudaSuccess;
+  for (int m = 0; m < e->count && ce == cudaSuccess; ++m) {
+    sgp_ctx* c = e->groups[e->member_group[m]];
+    const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+    ce = cudaMemcpyAsync((char*)c->field + (size_t)e->member_index[m] * bytes, host_in[m], bytes,
+                         cudaMemcpyHostToDevice, e->stream);
+  }
+  if (ce != cudaSuccess) {
+    cudaStreamSynchronize(e->stream);
+    return efail(e, SGP_ECUDA, "copy in: %s", cudaGetErrorString(ce));
+  }
+  e->t = t0;
+  for (sgp_ctx* g : e->groups) {
+    g->t = t0;
+    g->have_state = true;
+  }
+  e->have_state = true;
+  sgp_status st = SGP_OK;
+  if (nsteps > 0)
+    st = e->prec == SGP_F32 ? ens_run<float>(e, nsteps, dt, scheme)
+                            : ens_run<double>(e, nsteps, dt, scheme);
+  for (int m = 0; m < e->count && st == SGP_OK && ce == cudaSuccess; ++m) {
+    sgp_ctx* c = e->groups[e->member_group[m]];
+    const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+    ce = cudaMemcpyAsync(host_out[m], (const char*)c->field + (size_t)e->member_index[m] * bytes,
+                         bytes, cudaMemcpyDeviceToHost, e->stream);
+  }
+  const cudaError_t cs = cudaStreamSynchronize(e->stream);   // host buffers free after this
+  if (st != SGP_OK) return st;
+  if (ce == cudaSuccess) ce = cs;
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "copy out: %s", cudaGetErrorString(ce));
+  return SGP_OK;
+}
+
 sgp_status sgp_ensemble_step(sgp_ens* e, long long nsteps, double dt, int scheme) {
   if (!e) return SGP_EINVAL;
   if (nsteps < 0) return efail(e, SGP_EINVAL, "nsteps < 0");

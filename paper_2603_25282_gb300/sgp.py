@@ -88,6 +88,7 @@ def lib():
         "sgp_ensemble_set_member_state": (I, [P, I, P, I, D]),
         "sgp_ensemble_get_member_state": (I, [P, I, P, I]),
         "sgp_ensemble_step": (I, [P, LL, D, I]),
+        "sgp_ensemble_step_host": (I, [P, ctypes.POINTER(P), D, ctypes.POINTER(P), LL, D, I]),
         "sgp_ensemble_observables": (I, [P, ctypes.POINTER(Obs)]),
         "sgp_ensemble_synchronize": (I, [P]),
         "sgp_ensemble_launch_count": (LL, [P]),
@@ -547,6 +548,29 @@ class Ensemble:
     def step(self, nsteps, dt, scheme="ts2"):
         s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
         _echeck(lib().sgp_ensemble_step(self.handle, int(nsteps), float(dt), s), self.handle)
+
+    def step_host(self, srcs, t0, nsteps, dt, scheme="ts2", outs=None):
+        """Every member's state from host buffers srcs[m], nsteps steps, the
+        states to host buffers outs[m] (new arrays by default) in one call
+        (sgp_ensemble_step_host)."""
+        if len(srcs) != len(self.grids):
+            raise ValueError("one source buffer per member")
+        if outs is None:
+            outs = [np.empty((5,) + n[::-1], dtype=self.dtype) for n, _ in self.grids]
+        keep = []
+        pin = (ctypes.c_void_p * len(srcs))()
+        pout = (ctypes.c_void_p * len(srcs))()
+        for m, (a, b) in enumerate(zip(srcs, outs)):
+            pa, da, ka = _ptr(a, self.dtype)
+            pb, db, kb = _ptr(b, self.dtype)
+            if da or db:
+                raise ValueError("sgp_ensemble_step_host takes host buffers")
+            pin[m], pout[m] = pa, pb
+            keep += [ka, kb]
+        s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        _echeck(lib().sgp_ensemble_step_host(self.handle, pin, float(t0), pout, int(nsteps),
+                                             float(dt), s), self.handle)
+        return outs
 
     def autotune(self, reps=20, force=False):
         _echeck(lib().sgp_ensemble_autotune(self.handle, int(reps), SGP_TUNE_FORCE if force else 0),

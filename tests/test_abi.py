@@ -58,6 +58,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.sgp_record(None, 10, 0.1, 0, 0) == 1
     assert lib.sgp_set_health_check(None, 10, 1e-6) == 1
     assert lib.sgp_step_host(None, None, 0.0, None, 1, 0.1, 0, 1) == 1
+    assert lib.sgp_ensemble_step_host(None, None, 0.0, None, 1, 0.1, 0) == 1
     # allocator and free function come together
     assert lib.sgp_set_allocator(sgp.ALLOC_FN(lambda *a: None), sgp.FREE_FN(), None) == 1
     assert lib.sgp_set_allocator(sgp.ALLOC_FN(), sgp.FREE_FN(), None) == 0

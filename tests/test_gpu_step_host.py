@@ -92,3 +92,28 @@ def test_step_host_errors():
     out = c.step_host(psi, 0.0, 0, 1e-3, chunks=2)     # zero steps: a round trip
     assert np.array_equal(out, psi)
     c.close()
+
+
+def test_ensemble_step_host_equals_member_calls():
+    grids = [((32, 32), 6.0), ((48, 48), 7.0), ((32, 32), 6.0), ((64, 32), (8.0, 5.0))]
+    plist = _plist(len(grids))
+    psis = [inputs.gaussian_random_phase(n, L, seed=70 + k, amp=0.3).astype(np.complex64)
+            for k, (n, L) in enumerate(grids)]
+    with sgp.Ensemble(grids, prec="f32") as a, sgp.Ensemble(grids, prec="f32") as b:
+        a.set_params(plist)
+        b.set_params(plist)
+        for k, p in enumerate(psis):
+            a.set_member_state(k, p.copy(), 0.2)
+        a.step(9, 1e-3, "ts4")
+        ref = [a.get_member_state(k) for k in range(len(grids))]
+        srcs = [torch.from_numpy(p).pin_memory() for p in psis]
+        outs = b.step_host(srcs, 0.2, 9, 1e-3, "ts4")
+        for k in range(len(grids)):
+            assert np.array_equal(outs[k], ref[k]), k
+            assert np.array_equal(b.get_member_state(k), ref[k])
+        inplace = [p.copy() for p in psis]                 # pageable, in place
+        b.step_host(inplace, 0.2, 9, 1e-3, "ts4", outs=inplace)
+        for k in range(len(grids)):
+            assert np.array_equal(inplace[k], ref[k])
+        with pytest.raises(sgp.SgpError, match="EINVAL"):
+            b.step_host(psis, float("inf"), 1, 1e-3)
