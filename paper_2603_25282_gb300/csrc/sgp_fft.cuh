@@ -330,6 +330,23 @@ template <int DIR, typename C> struct Dft<6, DIR, C> {
 };
 
 // ----------------------------------------------------------------------------
+// barrier of the threads that share a set of exchange buffers
+// ----------------------------------------------------------------------------
+// GT = 0: the whole CTA; GT = 32: one warp; otherwise the GT threads (a
+// multiple of 32) that use named barrier `id` (1..15; 0 is the CTA's).
+template <int GT>
+__device__ __forceinline__ void group_sync(int id) {
+  if constexpr (GT == 0) {
+    __syncthreads();
+  } else if constexpr (GT == 32) {
+    __syncwarp();
+  } else {
+    static_assert(GT % 32 == 0, "named barriers count whole warps");
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(GT) : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Stockham stages over NC components held in registers
 // ----------------------------------------------------------------------------
 // v[c][e]: element i + T*e of component c's line.  tw: the stage twiddle
@@ -341,11 +358,11 @@ template <int DIR, typename C> struct Dft<6, DIR, C> {
 // them all (one more barrier before the next stage writes): the five
 // butterflies of a stage are independent work for the scheduler.  DIR = -1
 // forward, +1 inverse.  Every thread of the CTA must call this (barriers).
-template <typename R, int N, int E, int DIR, int NC, int NB, int S, int NS>
+template <typename R, int N, int E, int DIR, int NC, int NB, int S, int NS, int GT>
 struct FftStages {
   typedef cplx<R> C;
   __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const TwE<R>* tw,
-                                             C* buf0, int bstride) {
+                                             C* buf0, int bstride, int bid) {
     constexpr int RD = radix_at(N, E, S);
     if constexpr (RD > 0) {
       constexpr int T = N / E;
@@ -365,7 +382,7 @@ struct FftStages {
         }
       }
       // NB = NC: the previous stage's reads of the buffers must be done
-      if constexpr (!LAST && NB != 2 && S > 0) __syncthreads();
+      if constexpr (!LAST && NB != 2 && S > 0) group_sync<GT>(bid);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         C* buf = buf0 + (NB == 2 ? ((S * NC + c) & 1) : c) * bstride;
@@ -391,13 +408,13 @@ struct FftStages {
           }
         }
         if constexpr (!LAST && NB == 2) {
-          __syncthreads();
+          group_sync<GT>(bid);
 #pragma unroll
           for (int e = 0; e < E; ++e) v[c][e] = buf[padx<R>(i + T * e)];
         }
       }
       if constexpr (!LAST && NB != 2) {
-        __syncthreads();
+        group_sync<GT>(bid);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const C* buf = buf0 + c * bstride;
@@ -405,7 +422,7 @@ struct FftStages {
           for (int e = 0; e < E; ++e) v[c][e] = buf[padx<R>(i + T * e)];
         }
       }
-      FftStages<R, N, E, DIR, NC, NB, S + 1, NS * RD>::run(v, i, tw, buf0, bstride);
+      FftStages<R, N, E, DIR, NC, NB, S + 1, NS * RD, GT>::run(v, i, tw, buf0, bstride, bid);
     }
   }
 };
@@ -417,15 +434,15 @@ struct FftStages {
 // With the same rounded twiddle table, forward followed by this adjoint
 // equals N times the identity up to |W|^2 - 1 and butterfly rounding: the
 // twiddle phase errors cancel instead of accumulating over many steps.
-template <typename R, int N, int E, int NC, int NB, int S, int NS>
+template <typename R, int N, int E, int NC, int NB, int S, int NS, int GT>
 struct FftStagesAdj {
   typedef cplx<R> C;
   __device__ __forceinline__ static void run(C (&v)[NC][E], int i, const TwE<R>* tw,
-                                             C* buf0, int bstride) {
+                                             C* buf0, int bstride, int bid) {
     constexpr int RD = radix_at(N, E, S);
     if constexpr (RD > 0) {
       // later forward stages come first in the adjoint
-      FftStagesAdj<R, N, E, NC, NB, S + 1, NS * RD>::run(v, i, tw, buf0, bstride);
+      FftStagesAdj<R, N, E, NC, NB, S + 1, NS * RD, GT>::run(v, i, tw, buf0, bstride, bid);
       constexpr int T = N / E;
       constexpr int B = E / RD;
       constexpr bool LAST = (NS * RD == N);
@@ -442,14 +459,14 @@ struct FftStagesAdj {
         }
       }
       if constexpr (!LAST && NB != 2) {
-        if constexpr (!FIRSTBUF) __syncthreads();     // earlier reads of the buffers done
+        if constexpr (!FIRSTBUF) group_sync<GT>(bid);     // earlier reads of the buffers done
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           C* buf = buf0 + c * bstride;
 #pragma unroll
           for (int e = 0; e < E; ++e) buf[padx<R>(i + T * e)] = v[c][e];
         }
-        __syncthreads();
+        group_sync<GT>(bid);
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -457,7 +474,7 @@ struct FftStagesAdj {
         if constexpr (!LAST && NB == 2) {
 #pragma unroll
           for (int e = 0; e < E; ++e) buf[padx<R>(i + T * e)] = v[c][e];
-          __syncthreads();
+          group_sync<GT>(bid);
         }
 #pragma unroll
         for (int k = 0; k < B; ++k) {
@@ -487,17 +504,17 @@ struct FftStagesAdj {
 
 // Line transforms of NC components (forward DIR = -1, inverse +1); NB
 // exchange buffers of bstride elements from buf0 (see FftStages).
-template <typename R, int N, int E, int DIR, int NC, int NB>
+template <typename R, int N, int E, int DIR, int NC, int NB, int GT = 0>
 __device__ __forceinline__ void fft_lines(cplx<R> (&v)[NC][E], int i, const TwE<R>* tw,
-                                          cplx<R>* buf0, int bstride) {
+                                          cplx<R>* buf0, int bstride, int bid = 0) {
   static_assert(plan_ok(N, E), "no radix plan for this (N, E)");
   static_assert(NB == 2 || NB == NC, "two alternating buffers or one per component");
   // the previous user of the exchange buffers may still be reading
-  __syncthreads();
+  group_sync<GT>(bid);
   if constexpr (DIR < 0)
-    FftStages<R, N, E, -1, NC, NB, 0, 1>::run(v, i, tw, buf0, bstride);
+    FftStages<R, N, E, -1, NC, NB, 0, 1, GT>::run(v, i, tw, buf0, bstride, bid);
   else
-    FftStagesAdj<R, N, E, NC, NB, 0, 1>::run(v, i, tw, buf0, bstride);
+    FftStagesAdj<R, N, E, NC, NB, 0, 1, GT>::run(v, i, tw, buf0, bstride, bid);
 }
 
 }  // namespace sgp

@@ -343,23 +343,26 @@ struct XCfg {
   static constexpr int ROWS = (CT / T) > 0 ? (CT / T) : 1;
   static constexpr int THREADS = ROWS * T;
   static constexpr int LP = line_pad<R>(N);
-  static constexpr int NB = 5;                  // one exchange buffer per component (fits
-                                                // in the nonlinear staging area)
+  static constexpr int NB = 5;                  // one exchange buffer per component, which
+                                                // also stages the rows for the nonlinear flow
   static constexpr int XCH = NB * ROWS * LP;    // exchange buffers (complex)
-  static constexpr int STG = ROWS * 5 * N;      // nonlinear staging (complex)
-  static constexpr int BUF = XCH > STG ? XCH : STG;
+  static constexpr int BUF = XCH;
+  // rows wider than a warp synchronise their exchanges with a named barrier
+  // of their own (GT threads) instead of the CTA's
+  static constexpr int GT = (ROWS > 1 && ROWS < 16 && T % 32 == 0) ? T : 0;
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)BUF;
-  // two CTAs per SM when they fit in shared memory; four for the FP32
-  // half-size geometry (128 threads: at most 128 registers, a few spilled,
-  // measured 5% faster than three CTAs at ~160 registers)
-  static constexpr int MINB = (sizeof(R) == 4 && G == 1 && 4 * SMEM <= 220 * 1024) ? 4
-                              : (2 * SMEM <= 220 * 1024) ? 2 : 1;
+  // two CTAs per SM when they fit in shared memory
+  static constexpr int MINB = (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
 // x-pass: rows of all five components.  The nonlinear flow runs on the rows
 // staged in shared memory between the two transforms, as a plain loop over
 // points: one copy of its code (the unrolled form did not fit the
 // instruction cache) and registers only for the point being processed.
+// Each row's staging area is its own exchange buffers and each thread
+// stages, processes and reads back only the points it holds, so the rows
+// of a CTA synchronise independently (Cfg::GT) and the nonlinear flow needs
+// one barrier.
 template <typename R, int N, int E, int G>
 __global__ void __launch_bounds__(XCfg<R, N, E, G>::THREADS, XCfg<R, N, E, G>::MINB)
 k_xpass(XPassArgs<R> a) {
@@ -404,42 +407,43 @@ k_xpass(XPassArgs<R> a) {
 #pragma unroll
     for (int e = 0; e < E; ++e)
       v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
-  C* b0 = xb + g * Cfg::LP;
+  // twiddles, s_prm and s_yz come from other rows' threads
+  __syncthreads();
+  constexpr int GT = Cfg::GT;
+  const int bid = 1 + g;              // the row's named barrier when GT > 0
+  C* b0 = xb + g * Cfg::LP;           // the row's buffer of component c: b0 + c * bstride
   const int bstride = Cfg::ROWS * Cfg::LP;
-  if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
+  if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, bid);
   if (a.mode & XP_NL) {
-    C* stg = xb;                      // [ROWS][5][N], aliases the exchange buffers
-    __syncthreads();                  // exchange buffers free, s_prm visible
+    group_sync<GT>(bid);              // the row's exchange reads are done
 #pragma unroll
     for (int c = 0; c < 5; ++c)
 #pragma unroll
-      for (int e = 0; e < E; ++e) stg[(g * 5 + c) * N + i + T * e] = v[c][e];
-    __syncthreads();
+      for (int e = 0; e < E; ++e) b0[c * bstride + i + T * e] = v[c][e];
+    // no barrier: the thread processes exactly the points i + T e it staged
     const R co = s_prm[0], si = s_prm[1];
     const R c0p = s_prm[2], c1 = s_prm[3], c2 = s_prm[4];
     const R gx2h = s_prm[5], gy2h = s_prm[6], gz2h = s_prm[7];
 #pragma unroll 1
-    for (int pnt = threadIdx.x; pnt < Cfg::ROWS * N; pnt += Cfg::THREADS) {
-      const int gg = pnt / N, j = pnt - gg * N;
+    for (int j = i; j < N; j += T) {
+      const R y = s_yz[g][0];
+      const R zz = gz2h * s_yz[g][1] * s_yz[g][1];
       const R x = a.x0 + (R)j * a.hx;
-      const R y = s_yz[gg][0];
-      const R z = s_yz[gg][1];
       const R xr = co * x + si * y;
       const R yr = co * y - si * x;
-      const R V = gx2h * xr * xr + gy2h * yr * yr + gz2h * z * z;
-      C* pp = stg + gg * 5 * N + j;
-      C p[5] = {pp[0], pp[N], pp[2 * N], pp[3 * N], pp[4 * N]};
+      const R V = gx2h * xr * xr + gy2h * yr * yr + zz;
+      C* pp = b0 + j;
+      C p[5] = {pp[0], pp[bstride], pp[2 * bstride], pp[3 * bstride], pp[4 * bstride]};
       nonlinear_point<R>(p, V, a.delta, c0p, c1, c2);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) pp[c * N] = p[c];
+      for (int c = 0; c < 5; ++c) pp[c * bstride] = p[c];
     }
-    __syncthreads();
 #pragma unroll
     for (int c = 0; c < 5; ++c)
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[c][e] = stg[(g * 5 + c) * N + i + T * e];
+      for (int e = 0; e < E; ++e) v[c][e] = b0[c * bstride + i + T * e];
   }
-  if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
+  if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, bid);
   if (valid) {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
