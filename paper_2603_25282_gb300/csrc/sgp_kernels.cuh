@@ -351,8 +351,12 @@ struct XCfg {
   // of their own (GT threads) instead of the CTA's
   static constexpr int GT = (ROWS > 1 && ROWS < 16 && T % 32 == 0) ? T : 0;
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)BUF;
-  // two CTAs per SM when they fit in shared memory
-  static constexpr int MINB = (2 * SMEM <= 220 * 1024) ? 2 : 1;
+  // two CTAs per SM when they fit in shared memory; four for the FP32
+  // 128-thread geometry (at most 128 registers, a few spilled: 7% faster
+  // than the natural ~160 registers at N = 128, 2% slower at N = 512,
+  // where the autotuner prefers the 256-thread geometry anyway)
+  static constexpr int MINB = (sizeof(R) == 4 && G == 1 && 4 * SMEM <= 220 * 1024) ? 4
+                              : (2 * SMEM <= 220 * 1024) ? 2 : 1;
 };
 
 // x-pass: rows of all five components.  The nonlinear flow runs on the rows
