@@ -170,15 +170,22 @@ def test_f32_1000_steps_accuracy_and_mass():
 
 def test_f32_ts4_full_size_first_steps():
     """512^2 on [-16,16]^2, Omega = 0.9, gamma = 1.5, c = (1000,-5,10), TS4,
-    dt = 5e-4: the first two steps against the oracle (FP32 within 1e-5)."""
+    dt = 5e-4: the first two steps against the oracle (FP32 within 1e-5), in
+    every kernel plan the autotuner chooses between for this grid."""
     n, L = (512, 512), 16.0
     prm = _params(omega=0.9, gamma=1.5, c0=1000.0, c1=-5.0, c2=10.0)
     psi = inputs.gaussian_random_phase(n, L, seed=2, amp=0.01)
-    out32, _ = _gpu_run(n, L, prm, psi, 2, 5e-4, "ts4", "f32")
-    out64, _ = _gpu_run(n, L, prm, psi, 2, 5e-4, "ts4", "f64")
     ref, _ = _oracle_run(n, L, prm, psi, 2, 5e-4, "ts4")
+    out64, _ = _gpu_run(n, L, prm, psi, 2, 5e-4, "ts4", "f64")
     assert O.rel_l2(out64, ref) < 1e-10
-    assert O.rel_l2(out32, ref) < 1e-5
+    for plan in [(vx, vy) for vx in range(sgp.N_VARIANTS) for vy in range(sgp.N_VARIANTS)]:
+        c = _ctx(n, L, "f32", **prm)
+        c.set_plan(plan)
+        c.set_state(psi[None].astype(np.complex64).copy(), 0.0)
+        c.step(2, 5e-4, "ts4")
+        out32 = c.get_state()[0].astype(np.complex128)
+        c.close()
+        assert O.rel_l2(out32, ref) < 1e-5, plan
 
 
 # ----------------------------------------------------------------------------
@@ -377,8 +384,14 @@ def test_3d_128_full_size_first_steps():
         ref, _ = _oracle_run(n, L, prm, psi, 2, 1e-3, scheme)
         out64, _ = _gpu_run(n, L, prm, psi, 2, 1e-3, scheme, "f64")
         assert O.rel_l2(out64, ref) < 1e-10, scheme
-        out32, _ = _gpu_run(n, L, prm, psi, 2, 1e-3, scheme, "f32")
-        assert O.rel_l2(out32, ref) < 1e-5, scheme
+        for v in range(sgp.N_VARIANTS):          # every plan the autotuner tries per axis
+            c = _ctx(n, L, "f32", **prm)
+            c.set_plan((v, v, v))
+            c.set_state(psi[None].astype(np.complex64).copy(), 0.0)
+            c.step(2, 1e-3, scheme)
+            out32 = c.get_state()[0].astype(np.complex128)
+            c.close()
+            assert O.rel_l2(out32, ref) < 1e-5, (scheme, v)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
