@@ -85,14 +85,20 @@ def bytes_per_point_step(dim, scheme, prec):
     return 2 * s * passes * pairs, 2 * s
 
 
+# the sources that define the pass kernels and their launch geometry (the
+# host runtime in sgp_api.cu orchestrates them but does not change a launch's
+# traffic)
+KERNEL_SOURCES = ("sgp_fft.cuh", "sgp_kernels.cuh", "sgp_launch.cuh", "sgp_inst.cu")
+
+
 def csrc_hash():
-    """Hash of the CUDA sources (identifies the kernels the counters came from)."""
-    import glob
+    """Hash of the pass-kernel sources (identifies the kernels the counters
+    came from)."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2603_25282_gb300", "csrc", "*"))):
-        h.update(os.path.basename(p).encode())
-        with open(p, "rb") as f:
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2603_25282_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
