@@ -205,6 +205,23 @@ sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
  * before sgp_set_state; SGP_ECUDA if a launch fails. */
 sgp_status sgp_step(sgp_ctx* ctx, long long nsteps, double dt, int scheme);
 
+/* The substeps that nsteps steps of `scheme` issue (Sec. 3.3), host only
+ * (no device work): the per-step sequence of nonlinear ('N') and linear
+ * ('L') flows with the flows of the same kind that meet at a step boundary
+ * merged into one (N(a) N(b) = N(a + b) at equal time; L is
+ * time-independent in the rotating frame).  Entry k: kinds[k], its step
+ * deltas[k] and toffs[k], relative to the start of the run, the time at
+ * which a nonlinear flow acts or at which a linear one starts (time
+ * advances in the linear flows).  Writes the
+ * first min(cap, count) entries (arrays of cap elements, owned by the
+ * caller; may be NULL when cap = 0) and the total number of entries into
+ * *count.  sgp_step issues exactly this list (in chunks of 64 steps for
+ * graph replay, each chunk a list of its own).  Errors: SGP_EINVAL for an
+ * unknown scheme, nsteps < 0, dt <= 0 or non-finite, NULL count, or NULL
+ * arrays with cap > 0. */
+sgp_status sgp_substep_plan(int scheme, long long nsteps, double dt, long long cap, char* kinds,
+                            double* deltas, double* toffs, long long* count);
+
 /* Host-to-host propagation with the copies overlapped: the same result, bit
  * for bit, as sgp_set_state(ctx, host_in, 0, t0); sgp_step(ctx, nsteps,
  * dt, scheme); sgp_get_state(ctx, host_out, 0), but the batch is split into

@@ -604,8 +604,8 @@ struct SubRec {
 // meet at a step boundary merged: nonlinear flows at the same time (the flow
 // of Eq. (solution2) over a then b is the flow over a + b) and linear flows
 // (time-independent in the rotating frame, so L(a) L(b) = L(a + b)).  Time
-// advances in the linear substeps; the substep at the end of step s is at
-// (s + 1) dt.
+// advances in the linear substeps; a nonlinear substep at the end of step s
+// is at (s + 1) dt, a linear one carries its start time.
 std::vector<SubRec> merged_substeps(int scheme, long long n, double dt) {
   const auto seq = scheme_seq(scheme);
   std::vector<SubRec> subs;
@@ -614,7 +614,10 @@ std::vector<SubRec> merged_substeps(int scheme, long long n, double dt) {
     for (size_t k = 0; k < seq.size(); ++k) {
       const double delta = seq[k].second * dt;
       const char kind = seq[k].first;
-      const double toff = (k == seq.size() - 1) ? (double)(s + 1) * dt : (double)s * dt + sub * dt;
+      // a nonlinear flow acts at the current time (the end of step s exactly
+      // (s + 1) dt); a linear flow is stamped with its start time
+      const double toff = (kind == 'N' && k == seq.size() - 1) ? (double)(s + 1) * dt
+                                                                 : (double)s * dt + sub * dt;
       if (kind == 'L') sub += seq[k].second;
       if (k == 0 && !subs.empty() && subs.back().kind == kind)
         subs.back().delta += delta;        // meets the previous step's last substep
@@ -1695,6 +1698,22 @@ sgp_status sgp_step(sgp_ctx* c, long long nsteps, double dt, int scheme) {
                               : checked_steps<double>(c, nsteps, dt, scheme);
   return c->prec == SGP_F32 ? run_steps<float>(c, nsteps, dt, scheme)
                             : run_steps<double>(c, nsteps, dt, scheme);
+}
+
+sgp_status sgp_substep_plan(int scheme, long long nsteps, double dt, long long cap, char* kinds,
+                            double* deltas, double* toffs, long long* count) {
+  if (!count) return SGP_EINVAL;
+  *count = 0;
+  if (!valid_scheme(scheme) || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return SGP_EINVAL;
+  if (cap > 0 && (!kinds || !deltas || !toffs)) return SGP_EINVAL;
+  const std::vector<SubRec> subs = merged_substeps(scheme, nsteps, dt);
+  *count = (long long)subs.size();
+  for (long long k = 0; k < cap && k < *count; ++k) {
+    kinds[k] = subs[(size_t)k].kind;
+    deltas[k] = subs[(size_t)k].delta;
+    toffs[k] = subs[(size_t)k].toff;
+  }
+  return SGP_OK;
 }
 
 sgp_status sgp_step_host(sgp_ctx* c, const void* host_in, double t0, void* host_out,

@@ -100,6 +100,8 @@ def lib():
         "sgp_get_state_lab": (I, [P, P, I]),
         "sgp_step": (I, [P, LL, D, I]),
         "sgp_step_host": (I, [P, P, D, P, LL, D, I, I]),
+        "sgp_substep_plan": (I, [I, LL, D, LL, ctypes.c_char_p, ctypes.POINTER(D),
+                                 ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "sgp_substep": (I, [P, I, D]),
         "sgp_observables": (I, [P, ctypes.POINTER(Obs)]),
         "sgp_synchronize": (I, [P]),
@@ -250,6 +252,20 @@ def get_time(ctx):
 def step(ctx, nsteps, dt, scheme="ts2"):
     s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
     _check(lib().sgp_step(ctx, int(nsteps), float(dt), s), ctx)
+
+
+def substep_plan(scheme, nsteps, dt):
+    """sgp_substep_plan: [(kind, delta, time offset), ...] of a run (host only)."""
+    s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+    n = ctypes.c_longlong()
+    _check(lib().sgp_substep_plan(s, int(nsteps), float(dt), 0, None, None, None, ctypes.byref(n)))
+    cap = n.value
+    kinds = ctypes.create_string_buffer(max(cap, 1))
+    deltas = (ctypes.c_double * max(cap, 1))()
+    toffs = (ctypes.c_double * max(cap, 1))()
+    _check(lib().sgp_substep_plan(s, int(nsteps), float(dt), cap, kinds, deltas, toffs,
+                                  ctypes.byref(n)))
+    return [(kinds.raw[k:k + 1].decode(), deltas[k], toffs[k]) for k in range(n.value)]
 
 
 def step_host(ctx, src, t0, dst, nsteps, dt, scheme, chunks, dtype):
