@@ -57,7 +57,7 @@ typedef enum {
   SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up            */
   SGP_ENONFINITE = 5,    /* a NaN/Inf was detected in the observables     */
   SGP_ESTATE = 6,        /* call out of order (e.g. step before set_state)*/
-  SGP_EUNSUPPORTED = 7,  /* valid request this build does not implement   */
+  SGP_EUNSUPPORTED = 7,  /* valid request the library does not implement */
   SGP_EDRIFT = 8         /* the health check saw the mass drift too far   */
 } sgp_status;
 
