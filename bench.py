@@ -71,6 +71,14 @@ PAPER_EX2_SECONDS = {
     (3, "ts4"): {64: 172.46, 128: 1643.12, 192: 5671.32, 256: 14688.66},
 }
 PEFF_SIDES = {2: (64, 128, 192, 256), 3: (64, 128)}
+# FP64 passes are bound by the FP64 pipe, not by HBM.  DP arithmetic
+# instructions (DADD + DMUL + DFMA) per grid point of one launch, from the
+# counters of profiles/fp64_2d512_ts4.md (2D 512^2, plan 0,1), and the FP64
+# instruction peak: 1.25 TFLOP/s nominal = 2 DFMA per clock per SM, i.e.
+# 152 SMs x 2 x the maximum SM clock.
+FP64_DP_INSTR_PER_POINT = {("2d512_ts4_f64", "xpass"): 783, ("2d512_ts4_f64", "linepass_y"): 509}
+FP64_DP_PER_CLOCK_PER_SM = 2
+GB300_SMS = 152
 METRIC = "5-comp grid-pt*steps/s"
 GRAD_METRIC = "grads/s"
 L2_BYTES = 129 * 2 ** 20
@@ -353,6 +361,27 @@ def run_ours(args, rank, world, local_rank):
     dom_avg_ms = kinds[dom][1] / kinds[dom][0]
     achieved = per_pass_bytes / (dom_avg_ms * 1e-3) / 1e9
     traffic = measured_traffic(wl, dom, plan)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+            "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": traffic, "bytes_per_launch": per_pass_bytes, "avg_launch_ms": dom_avg_ms}
+    if (wl, dom) in FP64_DP_INSTR_PER_POINT:
+        # the FP64 path: the FP64 pipe is the binding roofline
+        clk_mhz = 2070.0
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                clk_mhz = float(json.load(f).get("sm_max_mhz", clk_mhz))
+        except Exception:
+            pass
+        dp_peak = GB300_SMS * FP64_DP_PER_CLOCK_PER_SM * clk_mhz * 1e6
+        dp_launch = FP64_DP_INSTR_PER_POINT[(wl, dom)] * pts * batch
+        dp_rate = dp_launch / (dom_avg_ms * 1e-3)
+        roof = {"bound": "alu", "kernel": dom, "achieved": dp_rate, "peak": dp_peak,
+                "peak_source": "nominal FP64 rate (1.25 TFLOP/s = 2 DFMA per clock per SM) "
+                               "at the maximum SM clock", "unit": "DP instr/s",
+                "frac": dp_rate / dp_peak, "traffic": traffic,
+                "dp_instr_per_launch": dp_launch, "avg_launch_ms": dom_avg_ms,
+                "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved / hbm_peak, "bytes_per_launch": per_pass_bytes}}
     bpp, bmin = bytes_per_point_step(dim, scheme, prec)
     step_gbs = bpp * pts * batch * args.steps / (ms * 1e-3) / 1e9
 
@@ -411,11 +440,8 @@ def run_ours(args, rank, world, local_rank):
                        "plan": plan, "tune_ms": tune_ms},
             "gpu_launches": launches,
             "clocks": clocks,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
-                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": traffic, "bytes_per_launch": per_pass_bytes,
-                         "avg_launch_ms": dom_avg_ms,
-                         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}},
+            "roofline": dict(roof, kernels={k: {"launches": v[0], "ms": v[1]}
+                                            for k, v in prof.items() if v[0]}),
             "step_hbm": {"algorithmic_bytes_per_point_step": bpp, "achieved_gbs": step_gbs,
                          "frac": step_gbs / hbm_peak,
                          "compulsory_bytes_per_point_step": bmin},
