@@ -64,3 +64,15 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.sgp_set_allocator(sgp.ALLOC_FN(), sgp.FREE_FN(), None) == 0
     assert lib.sgp_backward(None, None, 0, None, 0, None) == 1
     assert lib.sgp_destroy(None) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without libsgp.so every entry point of the binding raises."""
+    monkeypatch.setattr(sgp, "_lib", None)
+    monkeypatch.setattr(sgp, "LIB_PATH", str(tmp_path / "libsgp.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sgp.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        sgp.Context((32, 32), 4.0)
+    with pytest.raises(RuntimeError, match="not built"):
+        sgp.substep_plan("ts2", 1, 1e-3)
