@@ -112,10 +112,11 @@ typedef struct {
   double e_soc;         /* -gamma Psi^H S Psi                              */
 } sgp_obs;
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH.  Cannot fail. */
 int sgp_version(void);
 
-/* Human-readable name of a status code (static storage). */
+/* Human-readable name of a status code (static storage; "unknown"
+ * for a value outside the enum).  Cannot fail. */
 const char* sgp_status_string(sgp_status s);
 
 /* Create a context for `batch` independent fields on a dim-D grid
@@ -165,9 +166,11 @@ sgp_status sgp_set_allocator(sgp_alloc_fn alloc, sgp_free_fn free_fn, void* user
 sgp_status sgp_set_state(sgp_ctx* ctx, const void* src, int src_on_device,
                          double t0);
 
-/* Copy the current (rotating-frame) field out, same layout as set_state.
- * With dst_on_device == 0 the call synchronises the context stream before
- * returning; with a device pointer it is asynchronous. */
+/* Copy the current (rotating-frame) field out, same layout as set_state
+ * (the caller owns dst, batch*5*nz*ny*nx elements).  With dst_on_device ==
+ * 0 the call synchronises the context stream before returning; with a
+ * device pointer it is asynchronous.  Errors: SGP_EINVAL for NULL; SGP_ECUDA
+ * for a failed copy. */
 sgp_status sgp_get_state(sgp_ctx* ctx, void* dst, int dst_on_device);
 
 /* Lab-frame field at the current time t (Sec. 3.1): psi_l(x, t) =
@@ -186,7 +189,7 @@ sgp_status sgp_get_state(sgp_ctx* ctx, void* dst, int dst_on_device);
  * NULL dst, dim 1, or a non-square grid when quarter turns are needed. */
 sgp_status sgp_get_state_lab(sgp_ctx* ctx, void* dst, int dst_on_device);
 
-/* Current time t (host copy, FP64). */
+/* Current time t (host copy, FP64) into *t.  Errors: SGP_EINVAL for NULL. */
 sgp_status sgp_get_time(const sgp_ctx* ctx, double* t);
 
 /* Advance every batch member by nsteps steps of size dt with the given
@@ -253,7 +256,8 @@ sgp_status sgp_step_host(sgp_ctx* ctx, const void* host_in, double t0, void* hos
  * negative or non-finite drift_tol. */
 sgp_status sgp_set_health_check(sgp_ctx* ctx, long long every, double drift_tol);
 
-/* Enable (default) or disable graph replay in sgp_step. */
+/* Enable (default) or disable graph replay in sgp_step (results are the
+ * same either way).  Errors: SGP_EINVAL for a NULL ctx. */
 sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
 
 /* ---------------------------------------------------------------------
@@ -269,13 +273,15 @@ sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
  * compute the same transforms with different rounding (variant 3 has a
  * different radix plan), so results agree to rounding, not bit for bit.
  * ------------------------------------------------------------------- */
-/* 1 if variant v exists for line length n at precision prec, else 0. */
+/* 1 if variant v exists for line length n at precision prec, else 0
+ * (also for arguments out of range).  Cannot fail. */
 int sgp_variant_exists(int prec, int n, int variant);
 /* Set the plan: variants[a] for axis a < dim.  Synchronises the context
  * stream; drops captured graphs.  SGP_EINVAL for a variant that does not
  * exist (nothing is changed then). */
 sgp_status sgp_set_plan(sgp_ctx* ctx, const int* variants);
-/* Current plan into variants[0..2] (0 for absent axes). */
+/* Current plan into variants[0..2] (0 for absent axes; caller-owned array
+ * of 3).  Errors: SGP_EINVAL for NULL. */
 sgp_status sgp_get_plan(const sgp_ctx* ctx, int* variants);
 /* Autotuner: axis by axis (the other axes at their current variant), run
  * `reps` Strang steps (1..1000) of dt = 1e-3 with each variant of that
@@ -287,13 +293,15 @@ sgp_status sgp_get_plan(const sgp_ctx* ctx, int* variants);
  * has SGP_TUNE_FORCE or ms_out is given.  ms_out (may be NULL): 3 x 4
  * doubles, ms per step of [axis][variant], -1 where the variant or axis
  * does not exist.  Synchronises.  Allocates one field-sized scratch buffer
- * for the duration of the call. */
+ * for the duration of the call.  Errors: SGP_EINVAL for a NULL ctx or reps
+ * outside [1, 1000]; SGP_ENOMEM / SGP_ECUDA for the scratch or a launch. */
 sgp_status sgp_autotune(sgp_ctx* ctx, int reps, int flags, double* ms_out);
 
 /* Apply one substep of size delta (delta may be negative, Sec. 3.3 TS4):
  * SGP_SUB_NONLINEAR applies the exact flow (solution2) at the current time;
  * SGP_SUB_LINEAR applies the exact flow (sl1) and advances the time by delta.
- * Asynchronous. */
+ * Asynchronous.  Errors: SGP_EINVAL for a NULL ctx, an unknown kind or a
+ * non-finite delta; SGP_ESTATE before sgp_set_state; SGP_ECUDA. */
 sgp_status sgp_substep(sgp_ctx* ctx, int kind, double delta);
 
 /* Observables of Sec. 2 for every batch member into out[0..batch-1].
@@ -346,17 +354,23 @@ typedef struct sgp_ens sgp_ens;
  * stream as in sgp_create_grid.  Errors as sgp_create_grid per member. */
 sgp_status sgp_ensemble_create(int dim, int count, const int* n, const double* L,
                                int prec, int device, void* stream, sgp_ens** out);
-/* Number of grid groups. */
+/* Number of grid groups (0 for NULL). */
 int sgp_ensemble_groups(const sgp_ens* ens);
-/* p[0..count-1], one parameter set per member (synchronous). */
+/* p[0..count-1], one parameter set per member (synchronous).  Errors as
+ * sgp_set_params_batch, for the member group that fails. */
 sgp_status sgp_ensemble_set_params(sgp_ens* ens, const sgp_params* p);
 /* Copy member m's field (5*nz*ny*nx elements of its grid) in or out; layout
- * and on_device as sgp_set_state/sgp_get_state.  All members share t0. */
+ * and on_device as sgp_set_state/sgp_get_state (host copies synchronise).
+ * All members share t0.  Errors: SGP_EINVAL for NULL, a member out of
+ * range, a non-finite t0 or, once a state is set, a t0 other than the
+ * ensemble's time; SGP_ECUDA for a failed copy. */
 sgp_status sgp_ensemble_set_member_state(sgp_ens* ens, int member, const void* src,
                                          int src_on_device, double t0);
 sgp_status sgp_ensemble_get_member_state(sgp_ens* ens, int member, void* dst,
                                          int dst_on_device);
-/* Advance every member by nsteps steps (asynchronous). */
+/* Advance every member by nsteps steps (asynchronous).  Errors as
+ * sgp_step: SGP_EINVAL for nsteps < 0, dt <= 0 or non-finite, an unknown
+ * scheme; SGP_ESTATE before any member state; SGP_ECUDA. */
 sgp_status sgp_ensemble_step(sgp_ens* ens, long long nsteps, double dt, int scheme);
 /* Host round trip of the whole ensemble in one call: every member's state
  * from host_in[m] at time t0, nsteps steps, every member's state to
@@ -371,14 +385,21 @@ sgp_status sgp_ensemble_step(sgp_ens* ens, long long nsteps, double dt, int sche
  * SGP_ECUDA for a failed copy or launch. */
 sgp_status sgp_ensemble_step_host(sgp_ens* ens, const void* const* host_in, double t0,
                                   void* const* host_out, long long nsteps, double dt, int scheme);
-/* Observables of every member into out[0..count-1] (synchronises). */
+/* Observables of every member into out[0..count-1] (synchronises).
+ * Errors: SGP_EINVAL for NULL; SGP_ESTATE before any member state;
+ * SGP_ENONFINITE as sgp_observables (all members are still written). */
 sgp_status sgp_ensemble_observables(sgp_ens* ens, sgp_obs* out);
 /* sgp_autotune for every grid group of the ensemble (flags as there);
- * drops the ensemble's captured graphs. */
+ * drops the ensemble's captured graphs.  Errors as sgp_autotune. */
 sgp_status sgp_ensemble_autotune(sgp_ens* ens, int reps, int flags);
+/* Wait for the ensemble's work.  Errors: SGP_EINVAL for NULL; SGP_ECUDA. */
 sgp_status sgp_ensemble_synchronize(sgp_ens* ens);
+/* Kernels launched by the ensemble so far (0 for NULL). */
 long long sgp_ensemble_launch_count(const sgp_ens* ens);
+/* Message of the last failing call on ens, or of a failed creation for
+ * NULL; valid until the next call. */
 const char* sgp_ensemble_last_error(const sgp_ens* ens);
+/* Free the ensemble and its groups (synchronises first).  NULL is a no-op. */
 sgp_status sgp_ensemble_destroy(sgp_ens* ens);
 
 /* Allocation-free observables (no counterpart in the paper; a service of
@@ -414,10 +435,12 @@ sgp_status sgp_observables_static(int dim, const int* n, const double* L, int ba
                                   const void* field_dev, int device, void* stream,
                                   sgp_obs* out);
 
-/* Wait for all work issued on the context stream. */
+/* Wait for all work issued on the context stream.  Errors: SGP_EINVAL for
+ * NULL; SGP_ECUDA with the first asynchronous failure. */
 sgp_status sgp_synchronize(sgp_ctx* ctx);
 
-/* Number of kernels this context has launched so far (for accounting). */
+/* Number of kernels this context has launched so far (for accounting; graph
+ * replays count their kernels).  0 for NULL. */
 long long sgp_launch_count(const sgp_ctx* ctx);
 
 /* Per-kernel timing with CUDA events recorded on the context stream around
@@ -425,12 +448,14 @@ long long sgp_launch_count(const sgp_ctx* ctx);
  * 0 x-pass, 1 line pass along y, 2 line pass along z, 3 tables,
  * 4 observables, 5 other.  sgp_get_profile synchronises, writes the number
  * of launches and the summed device milliseconds of each kind into
- * launches[0..5] and ms[0..5], and clears the record.  Enabling clears too. */
+ * launches[0..5] and ms[0..5] (caller-owned arrays of 6), and clears the
+ * record.  Enabling clears too.  Graph replay is off while profiling.
+ * Errors: SGP_EINVAL for NULL; SGP_ECUDA. */
 sgp_status sgp_set_profiling(sgp_ctx* ctx, int enable);
 sgp_status sgp_get_profile(sgp_ctx* ctx, long long* launches, double* ms);
 
-/* Free the context and its device memory (synchronises first).  NULL is a
- * no-op. */
+/* Free the context and its device memory (synchronises first, through the
+ * allocator it was created with).  NULL is a no-op.  Always SGP_OK. */
 sgp_status sgp_destroy(sgp_ctx* ctx);
 
 /* Message of the last failing call on ctx ("" if none); static storage for

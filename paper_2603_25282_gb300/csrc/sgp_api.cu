@@ -2251,14 +2251,22 @@ sgp_status sgp_ensemble_observables(sgp_ens* e, sgp_obs* out) {
   if (!out) return efail(e, SGP_EINVAL, "NULL out");
   if (!e->have_state) return efail(e, SGP_ESTATE, "no state");
   DeviceGuard guard(e->device);
+  int first_bad = -1;
   for (size_t g = 0; g < e->groups.size(); ++g) {
     sgp_ctx* c = e->groups[g];
     std::vector<sgp_obs> tmp(c->batch);
     sgp_status st = sgp_observables(c, tmp.data());
     if (st != SGP_OK && st != SGP_ENONFINITE) return efail(e, st, "%s", c->err.c_str());
     for (int m = 0; m < e->count; ++m)
-      if (e->member_group[m] == (int)g) out[m] = tmp[e->member_index[m]];
+      if (e->member_group[m] == (int)g) {
+        out[m] = tmp[e->member_index[m]];
+        if (!std::isfinite(out[m].mass) || !std::isfinite(out[m].energy) ||
+            !std::isfinite(out[m].magnetization) || !std::isfinite(out[m].lz))
+          if (first_bad < 0 || m < first_bad) first_bad = m;
+      }
   }
+  // every member is written; a non-finite one is reported like sgp_observables
+  if (first_bad >= 0) return efail(e, SGP_ENONFINITE, "member %d: non-finite observables", first_bad);
   return SGP_OK;
 }
 

@@ -464,3 +464,16 @@ def test_health_check_reports_nonfinite_and_drift():
     c.set_health_check(0, 0.0)                   # off again
     c.step(20, 1e-3, "ts2")
     c.close()
+
+
+def test_ensemble_observables_report_a_nonfinite_member():
+    grids = [((32, 32), 6.0), ((48, 48), 7.0), ((32, 32), 6.0)]
+    with sgp.Ensemble(grids, prec="f32") as ens:
+        ens.set_params([_params()] * 3)
+        for k, (n, L) in enumerate(grids):
+            psi = inputs.gaussian_random_phase(n, L, seed=80 + k, amp=0.3).astype(np.complex64)
+            if k == 2:
+                psi[1, 5, 5] = np.nan
+            ens.set_member_state(k, psi, 0.0)
+        with pytest.raises(sgp.SgpError, match="ENONFINITE.*member 2"):
+            ens.observables()
