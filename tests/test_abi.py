@@ -76,3 +76,24 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         sgp.Context((32, 32), 4.0)
     with pytest.raises(RuntimeError, match="not built"):
         sgp.substep_plan("ts2", 1, 1e-3)
+
+
+def test_every_declaration_states_its_error_behaviour():
+    """Each entry point of include/sgp.h is documented with its errors (or
+    that it cannot fail); declarations written together share a comment."""
+    txt = open(os.path.join(ROOT, "include", "sgp.h")).read()
+    decl = re.compile(r"(?:sgp_status|int|long long|const char\*|void)\s+\**(sgp_[a-z_]+)\s*\([^;]*\);", re.S)
+    words = ("Error", "SGP_E", "Cannot fail", "for NULL", "no-op", "Always SGP_OK", "alid until")
+    missing = []
+    for m in decl.finditer(txt):
+        head = txt[:m.start()]
+        end = head.rfind("*/")
+        start = head.rfind("/*", 0, end)
+        between = head[end + 2:]
+        # only other declarations may sit between the comment and this one
+        if end < 0 or decl.sub("", between).strip():
+            missing.append(m.group(1))
+            continue
+        if not any(w in head[start:end] for w in words):
+            missing.append(m.group(1))
+    assert not missing, missing
