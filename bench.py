@@ -71,12 +71,12 @@ PAPER_EX2_SECONDS = {
     (3, "ts4"): {64: 172.46, 128: 1643.12, 192: 5671.32, 256: 14688.66},
 }
 PEFF_SIDES = {2: (64, 128, 192, 256), 3: (64, 128)}
-# FP64 passes are bound by the FP64 pipe, not by HBM.  DP arithmetic
-# instructions (DADD + DMUL + DFMA) per grid point of one launch, from the
-# counters of profiles/fp64_2d512_ts4.md (2D 512^2, plan 0,1), and the FP64
-# instruction peak: 1.25 TFLOP/s nominal = 2 DFMA per clock per SM, i.e.
-# 152 SMs x 2 x the maximum SM clock.
-FP64_DP_INSTR_PER_POINT = {("2d512_ts4_f64", "xpass"): 783, ("2d512_ts4_f64", "linepass_y"): 509}
+# FP64 passes are bound by the FP64 pipe, not by HBM: DP arithmetic
+# instructions (DADD + DMUL + DFMA) per grid point of one launch come from the
+# committed ncu counts (profiles/traffic.json, "dp_instr_per_point", valid
+# only for the kernels they were counted on); the FP64 instruction peak is
+# 1.25 TFLOP/s nominal = 2 DFMA per clock per SM, i.e. 152 SMs x 2 x the
+# maximum SM clock.
 FP64_DP_PER_CLOCK_PER_SM = 2
 GB300_SMS = 152
 METRIC = "5-comp grid-pt*steps/s"
@@ -121,6 +121,29 @@ def csrc_hash():
         with open(os.path.join(ROOT, "paper_2603_25282_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def measured_instr(wl, kernel, plan, key="thread_instr_per_point"):
+    """Instructions per grid point of one launch of `kernel` from the
+    committed ncu counts (thread instructions: executed warp instructions x
+    32 / points; or the FP64 arithmetic instructions), or None when the
+    kernels or the plan differ from the counted ones."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+    except Exception:
+        return None
+    if tr.get("csrc_sha256_16") != csrc_hash() or list(tr.get("plan", [])) != list(plan):
+        return None
+    return tr.get(key, {}).get("%s:%s" % (wl, kernel))
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 2070.0
 
 
 def measured_traffic(wl, kernel, plan):
@@ -242,12 +265,72 @@ def run_oracle_sample(wl, steps, warmup=1, budget=20.0):
     return pts * d["steps"] / d["seconds"], d
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_oracle_parallel(wl, procs, steps, warmup=1, budget=20.0):
+    """The oracle on `procs` members at once, one single-threaded process per
+    host core: all processes start together and each times its own steps;
+    the throughput is the points of all timed steps over the longest
+    process's timed wall time."""
+    n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = ORACLE_SNIPPET % {"root": ROOT, "args": repr((list(n), L, prm, scheme, dt, steps,
+                                                          warmup, budget))}
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+    res = []
+    for p in ps:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    pts = math.prod(n)
+    sec = max(d["seconds"] for d in res)
+    done = sum(d["steps"] for d in res)
+    return pts * done / sec, {"seconds": sec, "steps": done, "procs": procs}
+
+
 def cpu_baseline_block(wl, steps):
-    v, d = run_oracle_sample(wl, steps)
+    """The FP64 oracle on the host cores: one member on one thread, and one
+    member per core on all cores (nproc single-threaded processes)."""
+    v1, d1 = run_oracle_sample(wl, steps)
     n = WORKLOADS[wl][0]
-    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": "%d %s steps of one %s member (FP64 numpy oracle, 1 thread, %.1f s)"
-                      % (d["steps"], WORKLOADS[wl][3].upper(), "x".join(map(str, n)), d["seconds"])}
+    ncores = os.cpu_count() or 1
+    grid = "x".join(map(str, n))
+    blk = {"value": v1, "unit": METRIC, "cores": 1, "kind": "oracle", "nproc": ncores,
+           "cpu_model": cpu_model(),
+           "sample": "%d %s steps of one %s member (FP64 numpy oracle, 1 thread, %.1f s)"
+                     % (d1["steps"], WORKLOADS[wl][3].upper(), grid, d1["seconds"])}
+    if ncores > 1:
+        try:
+            va, da = run_oracle_parallel(wl, ncores, steps)
+            blk["single_thread"] = {"value": v1, "cores": 1, "sample": blk["sample"]}
+            blk.update(value=va, cores=ncores,
+                       sample="%d %s steps in all over %d concurrent single-threaded processes, one "
+                              "%s member each (FP64 numpy oracle, all %d cores, %.1f s)"
+                              % (da["steps"], WORKLOADS[wl][3].upper(), ncores, grid, ncores,
+                                 da["seconds"]))
+        except Exception as e:  # the single-thread figure stands
+            blk["all_cores_error"] = str(e)[:200]
+    return blk
 
 
 # ---------------------------------------------------------------------------
@@ -264,18 +347,23 @@ def run_reference(args, rank, world):
         print(json.dumps({"impl": "reference", "unavailable": why}))
         return 0
     n, L, prm, scheme, dt, prec, batch = WORKLOADS[wl]
-    # W untimed steps, then up to K timed steps within a bounded wall time
-    v, d = run_oracle_sample(wl, max(1, args.steps), args.warmup, budget=90.0)
+    # every host core runs one member (one single-threaded process each): W
+    # untimed steps, then up to K timed steps within a bounded wall time
+    ncores = os.cpu_count() or 1
+    v, d = run_oracle_parallel(wl, ncores, max(1, args.steps), args.warmup, budget=90.0)
+    per = d["steps"] / ncores
     line = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * d["seconds"] / d["steps"],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * d["seconds"] / per,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": wl, "grid": list(n), "scheme": scheme, "dt": dt,
-                       "members_timed": 1},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": "%d timed %s steps (after %d warm-up) of one member, FP64 "
-                                       "numpy oracle, 1 thread, %.1f s"
-                                       % (d["steps"], scheme.upper(), args.warmup, d["seconds"])},
+                       "members_timed": ncores},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": ncores, "kind": "oracle",
+                             "nproc": ncores, "cpu_model": cpu_model(),
+                             "sample": "%d timed %s steps in all (after %d warm-up each) over %d "
+                                       "concurrent single-threaded processes, one member each, FP64 "
+                                       "numpy oracle, %.1f s"
+                                       % (d["steps"], scheme.upper(), args.warmup, ncores, d["seconds"])},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -364,16 +452,25 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
             "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
             "traffic": traffic, "bytes_per_launch": per_pass_bytes, "avg_launch_ms": dom_avg_ms}
-    if (wl, dom) in FP64_DP_INSTR_PER_POINT:
+    ipp = measured_instr(wl, dom, plan)
+    if ipp is not None and prec == "f32":
+        # FP32 passes are bound by instruction issue: 4 schedulers per SM
+        # issue one warp instruction per clock each
+        issue_peak = GB300_SMS * 4 * sm_max_mhz() * 1e6
+        warp_instr = ipp * pts * batch / 32.0
+        roof["issue"] = {"bound": "issue", "achieved": warp_instr / (dom_avg_ms * 1e-3),
+                         "peak": issue_peak, "unit": "warp instr/s",
+                         "frac": warp_instr / (dom_avg_ms * 1e-3) / issue_peak,
+                         "thread_instr_per_point": ipp,
+                         "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock at "
+                                        "the maximum SM clock",
+                         "instr_source": "ncu executed warp instructions of one launch x 32 / points "
+                                         "(profiles/traffic.json)"}
+    dpp = measured_instr(wl, dom, plan, "dp_instr_per_point")
+    if dpp is not None:
         # the FP64 path: the FP64 pipe is the binding roofline
-        clk_mhz = 2070.0
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                clk_mhz = float(json.load(f).get("sm_max_mhz", clk_mhz))
-        except Exception:
-            pass
-        dp_peak = GB300_SMS * FP64_DP_PER_CLOCK_PER_SM * clk_mhz * 1e6
-        dp_launch = FP64_DP_INSTR_PER_POINT[(wl, dom)] * pts * batch
+        dp_peak = GB300_SMS * FP64_DP_PER_CLOCK_PER_SM * sm_max_mhz() * 1e6
+        dp_launch = dpp * pts * batch
         dp_rate = dp_launch / (dom_avg_ms * 1e-3)
         roof = {"bound": "alu", "kernel": dom, "achieved": dp_rate, "peak": dp_peak,
                 "peak_source": "nominal FP64 rate (1.25 TFLOP/s = 2 DFMA per clock per SM) "
@@ -455,10 +552,9 @@ def run_ours(args, rank, world, local_rank):
         }
         if acc is not None:
             line["accuracy"] = acc
-        print(json.dumps(line))
     ctx.close()
     rep.close()
-    return 0
+    return line if rank == 0 else None
 
 
 # ---------------------------------------------------------------------------
@@ -652,10 +748,9 @@ def run_grad(args, rank, world, local_rank):
                     "d2h_bytes_per_step": state_bytes + 5 * 8, "steps": e2e_n},
             "cpu_baseline": None,
         }
-        print(json.dumps(line))
     ctx.close()
     rep.close()
-    return 0
+    return line if rank == 0 else None
 
 
 # ---------------------------------------------------------------------------
@@ -688,8 +783,8 @@ def run_ens(args, rank, world, local_rank):
                                                              amp=0.01).astype(cdt))
     pts = sum(m["n"] ** 2 for m in members)
     sbytes = pts * 5 * (8 if cfg["prec"] == "f32" else 16)
-    if not args.no_tune:
-        ens.autotune(reps=10)
+    if not args.no_tune and not ens.persistent:
+        ens.autotune(reps=10)            # the persistent kernel has one fixed geometry
     ens.step(args.warmup, cfg["dt"], cfg["scheme"])
     torch.cuda.synchronize()
     rep.barrier()
@@ -735,6 +830,9 @@ def run_ens(args, rank, world, local_rank):
             "dtype": cfg["prec"], "data": "synthetic",
             "config": {"workload": wl, "members": cfg["count"], "sides": sides,
                        "groups": ens.groups, "points_per_step": pts, "scheme": cfg["scheme"],
+                       "persistent": ens.persistent,
+                       "launch": ("one persistent work-queue kernel per 64 steps (graph replay)"
+                                  if ens.persistent else "per-group pass launches as graph branches"),
                        "dt": cfg["dt"], "field_bytes_per_gpu": sbytes,
                        "l2": "field %.0f MB > L2 %.0f MB (inputs larger than L2)"
                              % (sbytes / 1e6, L2_BYTES / 1e6),
@@ -749,10 +847,9 @@ def run_ens(args, rank, world, local_rank):
                     "h2d_bytes_per_step": sbytes, "d2h_bytes_per_step": sbytes, "steps": e2e_n},
             "cpu_baseline": None,
         }
-        print(json.dumps(line))
     ens.close()
     rep.close()
-    return 0
+    return line if rank == 0 else None
 
 
 def run_peff(args, rank, world, local_rank):
@@ -831,6 +928,58 @@ def run_peff(args, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the other workloads, measured briefly in the default run (N = 1)
+# ---------------------------------------------------------------------------
+SUB_RUNS = (
+    # (workload, timed steps, warm-up steps)
+    ("3d128_ts2_f32", 100, 5),
+    ("ens256_ts2_f32", 50, 5),
+    ("grad256_ts2_f32", 2, 1),
+)
+
+
+def sub_workloads(args, local_rank):
+    """Short runs of the 128^3 TS2 workload, the 256-member ensemble and the
+    256^2 gradient workload in the same process, after the main measurement:
+    each block carries its value, its HBM fractions and (gradients) the
+    adjoint overhead; the full lines come from --workload <name>."""
+    out = {}
+    for wl, steps, warmup in SUB_RUNS:
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.steps, sub.warmup = wl, steps, warmup
+        sub.no_cpu, sub.no_accuracy, sub.batch, sub.plan = True, True, 0, ""
+        t0 = time.perf_counter()
+        try:
+            if wl in GRAD_WORKLOADS:
+                ln = run_grad(sub, 0, 1, local_rank)
+            elif wl in ENS_WORKLOADS:
+                ln = run_ens(sub, 0, 1, local_rank)
+            else:
+                ln = run_ours(sub, 0, 1, local_rank)
+        except Exception as e:  # the main number stands without it
+            out[wl] = {"error": str(e)[:300]}
+            continue
+        blk = {"metric": ln["metric"], "value": ln["value"], "unit": ln["unit"],
+               "steps": steps, "warmup": warmup, "ms_per_step": ln["ms_per_step"],
+               "dtype": ln["dtype"], "clocks": ln.get("clocks"),
+               "gpu_launches": ln.get("gpu_launches"),
+               "wall_s": time.perf_counter() - t0}
+        r = ln.get("roofline", {})
+        blk["roofline"] = {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac",
+                                                 "avg_launch_ms", "bytes_per_launch",
+                                                 "bytes_per_point_step") if k in r}
+        for k in ("step_hbm", "adjoint_overhead", "forward_ms", "e2e"):
+            if k in ln:
+                blk[k] = ln[k]
+        cfg = ln.get("config", {})
+        blk["config"] = {k: cfg[k] for k in ("grid", "members_per_gpu", "members", "sides", "scheme",
+                                             "plan", "points_per_step", "steps_per_gradient")
+                         if k in cfg}
+        out[wl] = blk
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -847,6 +996,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: skip the short runs of the 3D, ensemble and gradient workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -858,13 +1009,19 @@ def main():
             200 if args.workload in ENS_WORKLOADS else 500)
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload in GRAD_WORKLOADS:
-        return run_grad(args, rank, world, local_rank)
-    if args.workload in ENS_WORKLOADS:
-        return run_ens(args, rank, world, local_rank)
     if args.workload == "peff_example2":
         return run_peff(args, rank, world, local_rank)
-    return run_ours(args, rank, world, local_rank)
+    if args.workload in GRAD_WORKLOADS:
+        line = run_grad(args, rank, world, local_rank)
+    elif args.workload in ENS_WORKLOADS:
+        line = run_ens(args, rank, world, local_rank)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+        if line is not None and world == 1 and args.workload == "2d512_ts4_f32" and not args.no_sub:
+            line["workloads"] = sub_workloads(args, local_rank)
+    if line is not None:
+        print(json.dumps(line))
+    return 0
 
 
 if __name__ == "__main__":

@@ -54,7 +54,7 @@ typedef enum {
   SGP_EINVAL = 1,        /* bad argument (size, pointer, parameter, dt)   */
   SGP_ENOMEM = 2,        /* device or host allocation failed              */
   SGP_ECUDA = 3,         /* a CUDA runtime call failed (see last_error)   */
-  SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up            */
+  SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up (ensembles) */
   SGP_ENONFINITE = 5,    /* a NaN/Inf was detected in the observables     */
   SGP_ESTATE = 6,        /* call out of order (e.g. step before set_state)*/
   SGP_EUNSUPPORTED = 7,  /* valid request the library does not implement */
@@ -342,11 +342,24 @@ sgp_status sgp_backward(sgp_ctx* ctx, const void* g_T, int g_T_on_device, void* 
 
 /* ---------------------------------------------------------------------
  * Ensembles: independent runs on different grids advanced together.
- * Members are grouped by grid; each group is one batched context.  A step
- * of the ensemble issues every group's passes; runs of 64 steps or more
- * replay one captured CUDA graph per 64 steps in which the groups are
- * parallel branches.  All members share the time and the composition;
- * each has its own parameters.
+ * Members are grouped by grid; each group is one batched context.  All
+ * members share the time and the composition; each has its own
+ * parameters.
+ *
+ * 2D ensembles whose line lengths are all in {64, 96, 128, 192, 256, 384,
+ * 512} run in ONE persistent kernel launch per 64 steps (captured in a CUDA
+ * graph and replayed; a shorter rest is launched directly).  Its CTAs take
+ * work items, each one CTA tile of one pass (the x-pass with the nonlinear
+ * flow of Eq. (solution2), or the y-line pass with the linear flow of Eq.
+ * (sl1), Sec. 3) of one member, from a device queue ordered pass by pass;
+ * a per-member counter of finished tiles makes a member's pass wait for
+ * its previous passes.  Every such wait is bounded (sgp_ensemble_set_wait_
+ * limit); when one gives up the kernel stops and the step call returns
+ * SGP_ETIMEOUT.  The passes use the default kernel geometry (the autotuner's
+ * choices do not apply) and give the same results as the per-group launches
+ * with plan {0, 1}.  Other ensembles (3D, other line lengths, or with the
+ * persistent kernel switched off) issue every group's passes as parallel
+ * branches of one captured graph per 64 steps.
  * ------------------------------------------------------------------- */
 typedef struct sgp_ens sgp_ens;
 
@@ -368,10 +381,34 @@ sgp_status sgp_ensemble_set_member_state(sgp_ens* ens, int member, const void* s
                                          int src_on_device, double t0);
 sgp_status sgp_ensemble_get_member_state(sgp_ens* ens, int member, void* dst,
                                          int dst_on_device);
-/* Advance every member by nsteps steps (asynchronous).  Errors as
- * sgp_step: SGP_EINVAL for nsteps < 0, dt <= 0 or non-finite, an unknown
- * scheme; SGP_ESTATE before any member state; SGP_ECUDA. */
+/* Advance every member by nsteps steps.  Asynchronous, except with the
+ * persistent kernel, where the call waits for the work to finish so that
+ * it can report a wait that gave up.  Errors as sgp_step: SGP_EINVAL for
+ * nsteps < 0, dt <= 0 or non-finite, an unknown scheme; SGP_ESTATE before
+ * any member state; SGP_ECUDA; SGP_ETIMEOUT when a bounded device-side wait
+ * of the persistent kernel gave up (the members' states are then undefined
+ * and must be set again before the next step). */
 sgp_status sgp_ensemble_step(sgp_ens* ens, long long nsteps, double dt, int scheme);
+/* Use (enable = 1, the default when the ensemble qualifies) or not the
+ * persistent work-queue kernel for sgp_ensemble_step and
+ * sgp_ensemble_step_host.  Errors: SGP_EINVAL for NULL; SGP_EUNSUPPORTED to
+ * enable it for an ensemble that does not qualify (3D, or a line length it
+ * is not compiled for). */
+sgp_status sgp_ensemble_set_persistent(sgp_ens* ens, int enable);
+/* 1 if the steps run in the persistent kernel, else 0 (also for NULL). */
+int sgp_ensemble_persistent(const sgp_ens* ens);
+/* Limit of every device-side wait of the persistent kernel, in seconds of
+ * the GPU's nominal SM clock (default 1 s; at most 3600).  Errors:
+ * SGP_EINVAL for NULL or a limit outside (0, 3600]; SGP_ECUDA. */
+sgp_status sgp_ensemble_set_wait_limit(sgp_ens* ens, double seconds);
+/* Fault injection for tests of the bounded waits (no counterpart in the
+ * paper): in the next step call, the first work item of `member` does not
+ * signal its completion, so the member's second pass waits until the wait
+ * limit and the call returns SGP_ETIMEOUT.  Nothing traps or hangs; the
+ * ensemble stays usable once its states are set again.  Errors: SGP_EINVAL
+ * for NULL or a member out of range; SGP_EUNSUPPORTED when the persistent
+ * kernel is not in use. */
+sgp_status sgp_ensemble_inject_stall(sgp_ens* ens, int member);
 /* Host round trip of the whole ensemble in one call: every member's state
  * from host_in[m] at time t0, nsteps steps, every member's state to
  * host_out[m] (arrays of count pointers; member m's buffer holds its
@@ -421,15 +458,25 @@ sgp_status sgp_ensemble_destroy(sgp_ens* ens);
  * FP32); larger requests return SGP_EINVAL with a message.
  *
  * Arguments: the grid and precision as in sgp_create_grid; p the
- * parameters; t the time; field_dev a device pointer (on `device`) to
- * batch*5*nz*ny*nx elements in the layout of sgp_set_state, read only;
- * stream a cudaStream_t (or NULL); out[0..batch-1] host results.  The call
- * synchronises `stream`.  The first call on a device looks up the device
- * addresses of the scratch arrays (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call uses
- * the same scratch and overwrites what the previous call left there, so
- * calls that may overlap on the GPU (other streams, other host threads)
- * race and must be serialised by the caller. */
+ * parameters, one set applied to every member of the batch; t the time;
+ * field_dev a device pointer (on `device`) to batch*5*nz*ny*nx elements in
+ * the layout of sgp_set_state, read only; stream a cudaStream_t (or NULL);
+ * out[0..batch-1] host results.
+ *
+ * The first call on a device is a set-up: with that device current it looks
+ * up the device addresses of the scratch arrays (cudaGetSymbolAddress) and
+ * loads every kernel this entry point can launch, for all line lengths and
+ * both precisions.  CUDA loads a library's device code and file-scope
+ * arrays lazily, at first use, and that loading takes device memory; so
+ * make the first call while memory can still be allocated, as a warm-up.
+ * Every later call on that device allocates no device memory at all.
+ * No call may be made on a stream that is being captured: every call
+ * synchronises `stream` and copies the sums to host memory.  Every call
+ * uses the same scratch and overwrites what the previous call left there,
+ * so calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Errors (SGP_EINVAL for bad
+ * arguments or sizes beyond the limits, SGP_ECUDA, SGP_ENONFINITE for a
+ * non-finite observable) leave their message in sgp_last_error(NULL). */
 sgp_status sgp_observables_static(int dim, const int* n, const double* L, int batch,
                                   int prec, const sgp_params* p, double t,
                                   const void* field_dev, int device, void* stream,
@@ -458,8 +505,13 @@ sgp_status sgp_get_profile(sgp_ctx* ctx, long long* launches, double* ms);
  * allocator it was created with).  NULL is a no-op.  Always SGP_OK. */
 sgp_status sgp_destroy(sgp_ctx* ctx);
 
-/* Message of the last failing call on ctx ("" if none); static storage for
- * a NULL ctx (creation errors).  Valid until the next call on ctx. */
+/* Message of the last failing call on ctx ("" if none).  For a NULL ctx:
+ * the message of the last failing call made without a context
+ * (sgp_create_grid, sgp_set_allocator, sgp_ensemble_create,
+ * sgp_observables_static; all but sgp_set_allocator clear it when they
+ * start),
+ * in static storage.  Valid until the next call on ctx (or, for NULL, the
+ * next call without a context). */
 const char* sgp_last_error(const sgp_ctx* ctx);
 
 #ifdef __cplusplus

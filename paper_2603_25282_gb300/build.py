@@ -27,6 +27,8 @@ UNITS = [
     ("api", "sgp_api.cu", []),
     ("adjoint", "sgp_adjoint.cu", []),
     ("lab", "sgp_lab.cu", []),
+    ("persist_flo", "sgp_persist.cu", ["-DSGP_REAL=float", "-DSGP_PERSIST_DEFINE_SUPPORTED=1"]),
+    ("persist_dou", "sgp_persist.cu", ["-DSGP_REAL=double"]),
 ] + [
     ("inst_%s_%s_v%d" % (r[0:3], "xl"[part], v), "sgp_inst.cu",
      ["-DSGP_REAL=%s" % r, "-DSGP_PART=%d" % part, "-DSGP_VAR=%d" % v])

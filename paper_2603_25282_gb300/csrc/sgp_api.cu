@@ -17,6 +17,7 @@
 #include "sgp_adjoint.cuh"
 #include "sgp_lab.cuh"
 #include "sgp_launch.cuh"
+#include "sgp_persist.cuh"
 
 using namespace sgp;
 
@@ -269,6 +270,8 @@ struct sgp_ctx {
   bool shared_lin = true;           // all members share Omega and gamma
   bool have_state = false;
   std::vector<LinTables> tables;    // cache keyed by delta
+  long long tables_gen = 0;         // bumped whenever cached tables are freed
+  void* rec = nullptr;              // std::vector<PersistPass<R>>*: passes are recorded, not launched
   std::vector<GraphEntry> graphs;   // captured step chunks
   bool use_graphs = true;
   double* partials = nullptr;       // observables scratch
@@ -422,6 +425,7 @@ void free_tables(sgp_ctx* c) {
     dev_free(c, t.kz);
   }
   c->tables.clear();
+  c->tables_gen++;
 }
 
 // Copies the per-member parameters to the device (synchronous) and drops the
@@ -502,6 +506,19 @@ sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_o
   a.mp = c->mp_dev + c->win0;
   a.t_base = c->t_dev;
   a.t_off = t_off;
+  if (c->rec) {
+    // recorded for the persistent ensemble kernel (default radix plan)
+    PersistPass<R> p{};
+    a.tw = (const TwE<R>*)c->tw[0];
+    p.kind = PK_XPASS;
+    p.N = c->n[0];
+    const int rows = persist_xrows<R>(c->n[0]);
+    p.tiles = (a.rows + rows - 1) / rows;
+    p.members = window_members(c);
+    p.x = a;
+    static_cast<std::vector<PersistPass<R>>*>(c->rec)->push_back(p);
+    return SGP_OK;
+  }
   c->launches++;
   ProfScope ps(c, PK_X);
   SGP_CUDA(c, launch_xpass<R>(c->n[0], c->var[0], a, window_members(c), c->stream));
@@ -545,6 +562,19 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
     const double inv = 1.0 / ((double)c->n[0] * c->n[1] * (c->dim == 3 ? c->n[2] : 1));
     a.inv_hi = (R)inv;
     a.inv_lo = (R)(inv - (double)a.inv_hi);
+  }
+  if (c->rec) {
+    // recorded for the persistent ensemble kernel (2D: lines along y)
+    PersistPass<R> p{};
+    a.tw = (const TwE<R>*)c->tw[axis];
+    p.kind = PK_LINE;
+    p.N = c->n[axis];
+    const int tile = persist_ltile<R>(c->n[axis]);
+    p.tiles = ((a.nx + tile - 1) / tile) * planes;
+    p.members = window_members(c);
+    p.l = a;
+    static_cast<std::vector<PersistPass<R>>*>(c->rec)->push_back(p);
+    return SGP_OK;
   }
   c->launches++;
   ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
@@ -653,6 +683,7 @@ sgp_status emit_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
     }
   }
   if (xspec) SGP_TRY(x_pass<R>(c, XP_INV, 0.0, 0.0));
+  if (c->rec) return SGP_OK;           // recording passes only; the caller advances the time
   c->launches++;
   {
     ProfScope ps(c, PK_OTHER);
@@ -1933,6 +1964,27 @@ struct sgp_ens {
   bool have_state = false;
   long long launches = 0;
   std::string err;
+  // the persistent work-queue kernel (2D, line lengths of persist_supported)
+  bool persist_ok = false;          // every group can run in it
+  bool use_persist = true;
+  int persist_grid = 0;             // CTAs: the number that fit on the GPU at once
+  double wait_seconds = 1.0;        // limit of every device-side wait
+  long long wait_cycles = 0;
+  int* done_dev = nullptr;          // finished tiles of each member
+  PersistCtl* ctl_dev = nullptr;
+  std::vector<int> gbase;           // the first member (counter) of each group
+  struct PProg {
+    long long steps;
+    double dt;
+    int scheme;
+    std::vector<long long> gens;    // the groups' table generations it points at
+    void* dev;                      // PersistPass<R>[passes * groups]
+    PersistLayout lay;
+    long long nitems;
+    cudaGraphExec_t graph;          // captured launch (nullptr: launched directly)
+  };
+  std::vector<PProg> progs;
+  int stall_member = -1;            // test hook: withhold one completion signal
 };
 
 namespace {
@@ -2012,8 +2064,191 @@ sgp_status ens_graph(sgp_ens* e, long long steps, double dt, int scheme, cudaGra
   return SGP_OK;
 }
 
+void ens_free_progs(sgp_ens* e) {
+  for (auto& p : e->progs) {
+    if (p.graph) cudaGraphExecDestroy(p.graph);
+    dev_free(e->groups[0], p.dev);
+  }
+  e->progs.clear();
+}
+
+std::vector<long long> ens_table_gens(const sgp_ens* e) {
+  std::vector<long long> g;
+  for (const sgp_ctx* c : e->groups) g.push_back(c->tables_gen);
+  return g;
+}
+
+// The queue program of `steps` steps: every group's passes recorded from
+// emit_steps, interleaved pass by pass (all groups' items of pass 0, then of
+// pass 1, ...), and the layout the kernel decodes work items with.  Cached
+// per (steps, dt, scheme) while the tables it points at stay.
+template <typename R>
+sgp_status ens_persist_program(sgp_ens* e, long long steps, double dt, int scheme,
+                               sgp_ens::PProg** out) {
+  const std::vector<long long> gens = ens_table_gens(e);
+  for (auto& p : e->progs)
+    if (p.steps == steps && p.dt == dt && p.scheme == scheme && p.gens == gens) {
+      *out = &p;
+      return SGP_OK;
+    }
+  if (e->progs.size() >= 4) ens_free_progs(e);
+  const size_t G = e->groups.size();
+  std::vector<std::vector<PersistPass<R>>> per(G);
+  for (size_t g = 0; g < G; ++g) {
+    sgp_ctx* c = e->groups[g];
+    const cudaStream_t saved = c->stream;
+    c->stream = e->stream;
+    sgp_status st = ensure_tables<R>(c, dt, scheme);
+    c->rec = &per[g];
+    if (st == SGP_OK) st = emit_steps<R>(c, steps, dt, scheme);
+    c->rec = nullptr;
+    c->stream = saved;
+    if (st != SGP_OK) return efail(e, st, "group %zu: %s", g, c->err.c_str());
+  }
+  const size_t P = per[0].size();
+  for (size_t g = 1; g < G; ++g)
+    if (per[g].size() != P) return efail(e, SGP_EINVAL, "groups issue different pass sequences");
+  // passes alternate x-pass, line pass, ..., x-pass; the layout describes
+  // the items of one pass of each kind
+  sgp_ens::PProg pp{};
+  PersistLayout& lay = pp.lay;
+  lay.groups = (int)G;
+  lay.xoff[0] = lay.loff[0] = 0;
+  for (size_t p = 0; p < P; ++p)
+    for (size_t g = 0; g < G; ++g) {
+      const PersistPass<R>& q = per[g][p];
+      if (q.kind != (p % 2 ? PK_LINE : PK_XPASS) || P % 2 == 0)
+        return efail(e, SGP_EINVAL, "unexpected pass sequence for the persistent kernel");
+      int& t = q.kind == PK_XPASS ? lay.xt[g] : lay.lt[g];
+      if (p < 2) t = q.tiles;
+      else if (t != q.tiles) return efail(e, SGP_EINVAL, "passes of one kind differ in tiles");
+    }
+  for (size_t g = 0; g < G; ++g) {
+    lay.xi[g] = (lay.xt[g] + kTilesPerItem - 1) / kTilesPerItem;
+    lay.li[g] = (lay.lt[g] + kTilesPerItem - 1) / kTilesPerItem;
+    lay.xoff[g + 1] = lay.xoff[g] + per[g][0].members * lay.xi[g];
+    lay.loff[g + 1] = lay.loff[g] + per[g][0].members * (P > 1 ? lay.li[g] : 0);
+    lay.base[g] = e->gbase[g];
+  }
+  lay.IX = lay.xoff[G];
+  lay.IL = lay.loff[G];
+  std::vector<PersistPass<R>> prog;
+  prog.reserve(P * G);
+  for (size_t p = 0; p < P; ++p)
+    for (size_t g = 0; g < G; ++g) prog.push_back(per[g][p]);
+  const long long item = (long long)(P / 2) * (lay.IX + lay.IL) + lay.IX;
+  if (item >= (1LL << 31)) return efail(e, SGP_EUNSUPPORTED, "too many work items for one launch");
+  const size_t bytes = prog.size() * sizeof(PersistPass<R>);
+  cudaError_t ce = dev_alloc(e->groups[0], &pp.dev, bytes);
+  if (ce != cudaSuccess) return efail(e, SGP_ENOMEM, "persistent program: %s", cudaGetErrorString(ce));
+  ce = cudaMemcpy(pp.dev, prog.data(), bytes, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    dev_free(e->groups[0], pp.dev);
+    return efail(e, SGP_ECUDA, "persistent program: %s", cudaGetErrorString(ce));
+  }
+  pp.steps = steps;
+  pp.dt = dt;
+  pp.scheme = scheme;
+  pp.gens = ens_table_gens(e);       // after ensure_tables: the tables recorded above
+  pp.nitems = item;
+  pp.graph = nullptr;
+  e->progs.push_back(pp);
+  *out = &e->progs.back();
+  return SGP_OK;
+}
+
+// One launch of a program on the ensemble stream: the queue head and the
+// completion counters cleared, the persistent kernel, every group's time
+// advanced.
+template <typename R>
+sgp_status ens_persist_issue(sgp_ens* e, const sgp_ens::PProg& p) {
+  cudaError_t ce = cudaMemsetAsync(&e->ctl_dev->head, 0, sizeof(unsigned long long), e->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(e->done_dev, 0, sizeof(int) * (size_t)e->count, e->stream);
+  if (ce == cudaSuccess)
+    ce = launch_persistent<R>((const PersistPass<R>*)p.dev, p.lay, (int)p.nitems, e->done_dev, e->ctl_dev,
+                              e->wait_cycles, e->persist_grid, e->stream);
+  for (sgp_ctx* c : e->groups)
+    if (ce == cudaSuccess) {
+      k_add_time<<<1, 1, 0, e->stream>>>(c->t_dev, (double)p.steps * p.dt);
+      ce = cudaGetLastError();
+    }
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "persistent launch: %s", cudaGetErrorString(ce));
+  return SGP_OK;
+}
+
+// nsteps steps through the persistent kernel: one captured launch per chunk
+// of kGraphChunk steps, the rest launched directly; then the control word:
+// SGP_ETIMEOUT if a wait gave up (the call synchronises for this).
+template <typename R>
+sgp_status ens_run_persistent(sgp_ens* e, long long nsteps, double dt, int scheme) {
+  // control word: no failure, no withheld signal (all bytes 0xff = -1)
+  cudaError_t ce = cudaMemsetAsync(&e->ctl_dev->err, 0, 16, e->stream);   // err, pad, err_item
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(&e->ctl_dev->withhold, 0xff, sizeof(long long), e->stream);
+  long long done = 0;
+  while (ce == cudaSuccess && done < nsteps) {
+    const long long steps = nsteps - done >= kGraphChunk ? kGraphChunk : nsteps - done;
+    sgp_ens::PProg* p = nullptr;
+    SGP_TRY(ens_persist_program<R>(e, steps, dt, scheme, &p));
+    const bool stall = done == 0 && e->stall_member >= 0;
+    if (stall) {
+      // the member's first work item (pass 0) will not signal its completion
+      const int g = e->member_group[e->stall_member];
+      const long long withhold = p->lay.xoff[g] + (long long)e->member_index[e->stall_member] * p->lay.xi[g];
+      ce = cudaMemcpyAsync(&e->ctl_dev->withhold, &withhold, sizeof(long long), cudaMemcpyHostToDevice,
+                           e->stream);      // pageable source: staged before the call returns
+      if (ce != cudaSuccess) break;
+    }
+    if (steps == kGraphChunk && !p->graph) {
+      ce = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) break;
+      sgp_status st = ens_persist_issue<R>(e, *p);
+      cudaGraph_t graph = nullptr;
+      ce = cudaStreamEndCapture(e->stream, &graph);
+      if (st != SGP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ce != cudaSuccess) break;
+      ce = cudaGraphInstantiate(&p->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) break;
+    }
+    if (p->graph) {
+      ce = cudaGraphLaunch(p->graph, e->stream);
+    } else {
+      SGP_TRY(ens_persist_issue<R>(e, *p));
+    }
+    if (ce == cudaSuccess && stall)
+      ce = cudaMemsetAsync(&e->ctl_dev->withhold, 0xff, sizeof(long long), e->stream);
+    e->launches += 1 + (long long)e->groups.size();
+    done += steps;
+  }
+  PersistCtl ctl{};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&ctl, e->ctl_dev, sizeof ctl, cudaMemcpyDeviceToHost, e->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+  e->stall_member = -1;
+  e->t += (double)nsteps * dt;
+  for (sgp_ctx* c : e->groups) c->t = e->t;
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "persistent run: %s", cudaGetErrorString(ce));
+  if (ctl.err) {
+    e->have_state = false;
+    return efail(e, SGP_ETIMEOUT,
+                 "a device-side wait gave up after %.3g s (work item %lld); the members' states are "
+                 "undefined until they are set again",
+                 e->wait_seconds, ctl.err_item);
+  }
+  return SGP_OK;
+}
+
 template <typename R>
 sgp_status ens_run(sgp_ens* e, long long nsteps, double dt, int scheme) {
+  if (e->persist_ok && e->use_persist) {
+    for (sgp_ctx* c : e->groups) {
+      k_set_time<<<1, 1, 0, e->stream>>>(c->t_dev, e->t);
+      e->launches++;
+    }
+    return ens_run_persistent<R>(e, nsteps, dt, scheme);
+  }
   for (sgp_ctx* c : e->groups) {
     k_set_time<<<1, 1, 0, e->stream>>>(c->t_dev, e->t);
     e->launches++;
@@ -2124,17 +2359,75 @@ sgp_status sgp_ensemble_create(int dim, int count, const int* n, const double* L
     e->groups.push_back(c);
   }
   cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+  // the persistent work-queue kernel: 2D ensembles whose every line length
+  // it is compiled for
+  int base = 0;
+  for (sgp_ctx* c : e->groups) {
+    e->gbase.push_back(base);
+    base += c->batch;
+  }
+  bool ok = dim == 2 && (int)e->groups.size() <= kPersistMaxGroups;
+  for (sgp_ctx* c : e->groups) ok = ok && persist_supported(c->n[0]) && persist_supported(c->n[1]);
+  if (ok) {
+    int bps = 0, sms = 0, khz = 0;
+    ce = prec == SGP_F32 ? persist_prepare<float>(&bps) : persist_prepare<double>(&bps);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+    if (ce == cudaSuccess && bps > 0) ce = dev_alloc(e->groups[0], (void**)&e->done_dev, sizeof(int) * count);
+    if (ce == cudaSuccess && bps > 0) ce = dev_alloc(e->groups[0], (void**)&e->ctl_dev, sizeof(PersistCtl));
+    if (ce != cudaSuccess) {
+      sgp_ensemble_destroy(e);
+      return efail(nullptr, SGP_ECUDA, "persistent kernel set-up: %s", cudaGetErrorString(ce));
+    }
+    e->persist_ok = bps > 0;
+    e->persist_grid = bps * sms;
+    if (khz <= 0) khz = 2000000;        // the limit is approximate: assume 2 GHz if unknown
+    e->wait_cycles = (long long)(e->wait_seconds * khz * 1e3);
+  }
   *out = e;
   return SGP_OK;
 }
 
 int sgp_ensemble_groups(const sgp_ens* e) { return e ? (int)e->groups.size() : 0; }
 
+sgp_status sgp_ensemble_set_persistent(sgp_ens* e, int enable) {
+  if (!e) return SGP_EINVAL;
+  if (enable && !e->persist_ok)
+    return efail(e, SGP_EUNSUPPORTED, "the persistent kernel needs a 2D ensemble of at most 32 grids "
+                                      "with line lengths in {64, 96, 128, 192, 256, 384, 512}");
+  e->use_persist = enable != 0;
+  return SGP_OK;
+}
+
+int sgp_ensemble_persistent(const sgp_ens* e) { return e && e->persist_ok && e->use_persist ? 1 : 0; }
+
+sgp_status sgp_ensemble_set_wait_limit(sgp_ens* e, double seconds) {
+  if (!e) return SGP_EINVAL;
+  if (!(seconds > 0.0) || !std::isfinite(seconds) || seconds > 3600.0)
+    return efail(e, SGP_EINVAL, "wait limit must be in (0, 3600] seconds");
+  int khz = 0;
+  cudaError_t ce = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, e->device);
+  if (ce != cudaSuccess) return efail(e, SGP_ECUDA, "%s", cudaGetErrorString(ce));
+  if (khz <= 0) khz = 2000000;
+  e->wait_seconds = seconds;
+  e->wait_cycles = (long long)(seconds * khz * 1e3);
+  return SGP_OK;
+}
+
+sgp_status sgp_ensemble_inject_stall(sgp_ens* e, int member) {
+  if (!e) return SGP_EINVAL;
+  if (member < 0 || member >= e->count) return efail(e, SGP_EINVAL, "member %d out of range", member);
+  if (!(e->persist_ok && e->use_persist)) return efail(e, SGP_EUNSUPPORTED, "the persistent kernel is not in use");
+  e->stall_member = member;
+  return SGP_OK;
+}
+
 sgp_status sgp_ensemble_set_params(sgp_ens* e, const sgp_params* p) {
   if (!e) return SGP_EINVAL;
   if (!p) return efail(e, SGP_EINVAL, "NULL params");
   DeviceGuard guard(e->device);
   ens_free_graphs(e);
+  ens_free_progs(e);
   for (size_t g = 0; g < e->groups.size(); ++g) {
     sgp_ctx* c = e->groups[g];
     std::vector<sgp_params> sub(c->batch);
@@ -2298,6 +2591,11 @@ sgp_status sgp_ensemble_destroy(sgp_ens* e) {
   DeviceGuard guard(e->device);
   if (e->stream) cudaStreamSynchronize(e->stream);
   ens_free_graphs(e);
+  if (!e->groups.empty()) {
+    ens_free_progs(e);
+    dev_free(e->groups[0], e->done_dev);
+    dev_free(e->groups[0], e->ctl_dev);
+  }
   for (sgp_ctx* c : e->groups) sgp_destroy(c);
   for (cudaStream_t s : e->gstreams) cudaStreamDestroy(s);
   for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
@@ -2345,8 +2643,30 @@ sgp_status static_fail(sgp_status s, const char* fmt, ...) {
   return s;
 }
 
-// Device addresses of the scratch arrays for the current device (set-up on
-// the first call per device).
+// Load every kernel sgp_observables_static can launch (all line lengths,
+// both precisions) on the current device.  CUDA loads kernels lazily, at
+// their first use, and loading places their code in device memory; doing it
+// here, in the set-up, leaves nothing to load (or allocate) in later calls.
+// cudaFuncSetAttribute (inside the prepare_* calls) and cudaFuncGetAttributes
+// load the function they are given.
+cudaError_t static_preload_kernels() {
+  cudaError_t e = cudaSuccess;
+#define SGP_PRELOAD(N)                                                         \
+  if (e == cudaSuccess) e = prepare_xpass<float>(N);                           \
+  if (e == cudaSuccess) e = prepare_linepass<float>(N);                        \
+  if (e == cudaSuccess) e = prepare_xpass<double>(N);                          \
+  if (e == cudaSuccess) e = prepare_linepass<double>(N);
+  SGP_FOR_EACH_N(SGP_PRELOAD)
+#undef SGP_PRELOAD
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_reduce_partials);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_twiddles_f32);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_twiddles_f64);
+  return e;
+}
+
+// Device addresses of the scratch arrays for the current device, and every
+// kernel loaded (set-up on the first call per device).
 sgp_status static_scratch(int device, StaticScratch** out) {
   if (device < 0 || device >= kMaxDevices) return static_fail(SGP_EINVAL, "device %d out of range", device);
   if (!g_scratch_ready[device]) {
@@ -2357,6 +2677,8 @@ sgp_status static_scratch(int device, StaticScratch** out) {
         (e = cudaGetSymbolAddress(&sc.tw, g_static_tw)) != cudaSuccess ||
         (e = cudaGetSymbolAddress((void**)&sc.prm, g_static_prm)) != cudaSuccess)
       return static_fail(SGP_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    if ((e = static_preload_kernels()) != cudaSuccess)
+      return static_fail(SGP_ECUDA, "loading the observables kernels: %s", cudaGetErrorString(e));
     g_scratch[device] = sc;
     g_scratch_ready[device] = true;
   }

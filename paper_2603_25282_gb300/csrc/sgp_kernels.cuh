@@ -266,10 +266,45 @@ __device__ __forceinline__ bool spin_rotation(R Fz, cplx<R> Fp, R c1, R delta, S
 // ----------------------------------------------------------------------------
 // exact nonlinear flow at one point (Sec. 3.2, Eq. (solution2))
 // ----------------------------------------------------------------------------
+// (F.f) u with the spin-2 matrices of Sec. 1: tridiagonal, diagonal
+// (2, 1, 0, -1, -2) Fz, F- = conj(F+) above and F+ below the diagonal,
+// times sqrt(6)/2 next to the middle row.  Fz and Fp may carry a common
+// real factor.
+template <typename R>
+__device__ __forceinline__ void spin_dot(R Fz, cplx<R> Fp, const cplx<R> (&u)[5], cplx<R> (&o)[5]) {
+  typedef cplx<R> C;
+  const C sFp = cscale(Fp, (R)1.22474487139158904910);
+  const R Fz2 = (R)2 * Fz;
+  o[0] = cadd(cscale(u[0], Fz2), cconjmul(Fp, u[1]));
+  o[1] = cadd(cadd(cmul(Fp, u[0]), cscale(u[1], Fz)), cconjmul(sFp, u[2]));
+  o[2] = cadd(cmul(sFp, u[1]), cconjmul(sFp, u[3]));
+  o[3] = cadd(csub(cmul(sFp, u[2]), cscale(u[3], Fz)), cconjmul(Fp, u[4]));
+  o[4] = csub(cmul(Fp, u[3]), cscale(u[4], Fz2));
+}
+
+// Two functions of x = a^2 by their Taylor series (for x < 0.25, i.e.
+// |a| < 0.5, the remainders are below 3e-11 relative, far below FP32
+// rounding, and both keep full relative accuracy for small a, which the
+// increment forms need): sinc_sq(x) = sin(a)/a, cosm1_sq(x) = cos(a) - 1.
+__device__ __forceinline__ float sinc_sq(float x) {
+  float p = fmaf(x, 2.7557319e-6f, -1.9841270e-4f);   // 1/9!, -1/7!
+  p = fmaf(x, p, 8.3333333e-3f);                       // 1/5!
+  p = fmaf(x, p, -1.6666667e-1f);                      // -1/3!
+  return fmaf(x, p, 1.0f);
+}
+__device__ __forceinline__ float cosm1_sq(float x) {
+  float p = fmaf(x, -2.7557319e-7f, 2.4801587e-5f);   // -1/10!, 1/8!
+  p = fmaf(x, p, -1.3888889e-3f);                      // -1/6!
+  p = fmaf(x, p, 4.1666667e-2f);                       // 1/4!
+  p = fmaf(x, p, -0.5f);                               // -1/2!
+  return x * p;
+}
+
 template <typename R>
 __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
                                                 R c0p, R c1, R c2) {
   typedef cplx<R> C;
+  constexpr bool F32 = sizeof(R) == 4;
   const R r6 = (R)2.44948974278317809820;
   const R rs5 = (R)0.44721359549995793928;   // 1/sqrt(5)
   const R a0 = cabs2(v[0]), a1 = cabs2(v[1]), a2 = cabs2(v[2]);
@@ -283,18 +318,32 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
   C A00 = csub(cmul(v[0], v[4]), cmul(v[1], v[3]));
   A00 = cscale(cadd(cscale(A00, (R)2), cmul(v[2], v[2])), rs5);
   // (1) singlet-pair rotation, as the increment of
-  //     b = cos(c2 S d) Psi + i sin(c2 S d)/S (rho/5 Psi - A00 A conj(Psi)),
-  //     cos - 1 = -2 sin^2(c2 S d / 2), sin(c2 S d)/S = 2 sin cos (half angle) / S
+  //     b = cos(th) Psi + i sin(th)/S (rho/5 Psi - A00 A conj(Psi)),
+  //     th = c2 S d, S^2 = rho^2/25 - |A00|^2/5
   const R S2 = rho * rho * (R)0.04 - cabs2(A00) * (R)0.2;
-  R S = (R)0, rS = (R)0;
-  if (S2 > (R)0) {
-    rS = rsqrt_r(S2);
-    S = S2 * rS;
+  R cm1, sinc;       // cos(th) - 1 and sin(th)/S
+  const R th2 = c2 * delta * c2 * delta * (S2 > (R)0 ? S2 : (R)0);
+  if (F32 && th2 < (R)0.25) {
+    // half-angle series in u = (th/2)^2, no square root: sh = sin(th/2) =
+    // (th/2) q, ch = cos(th/2); cm1 = -2 sh^2, sin(th)/S = 2 sh ch / S =
+    // c2 d q ch.  As in the form below, (1 + cm1)^2 + (sinc S)^2 - 1 =
+    // -4 sh^2 (1 - sh^2 - ch^2): the rounding of the series enters the norm
+    // only times sh^2.
+    const float u = 0.25f * (float)th2;
+    const R q = (R)sinc_sq(u), ch = (R)1 + (R)cosm1_sq(u);
+    cm1 = (R)-2 * (R)u * q * q;
+    sinc = c2 * delta * q * ch;
+  } else {
+    R S = (R)0, rS = (R)0;
+    if (S2 > (R)0) {
+      rS = rsqrt_r(S2);
+      S = S2 * rS;
+    }
+    R sh1, ch1;
+    sincos_small((R)0.5 * c2 * S * delta, &sh1, &ch1);
+    cm1 = (R)-2 * sh1 * sh1;
+    sinc = S > (R)0 ? (R)2 * sh1 * ch1 * rS : c2 * delta;
   }
-  R sh1, ch1;
-  sincos_small((R)0.5 * c2 * S * delta, &sh1, &ch1);
-  const R cm1 = (R)-2 * sh1 * sh1;
-  const R sinc = S > (R)0 ? (R)2 * sh1 * ch1 * rS : c2 * delta;
   // increment = (cm1 + i sinc rho/5) Psi - (i sinc A00/sqrt5) (sqrt5 A conj(Psi)),
   // sqrt5 A conj(Psi) = (conj m2, -conj m1, conj p0, -conj p1, conj p2)
   const C al = mkc(cm1, sinc * rho * (R)0.2);
@@ -309,10 +358,33 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
       b[k] = cadd(v[k], inc[k]);
     }
   }
-  // (2) spin rotation exp(-i c1 d F.f), applied as the increment of the
-  //     spin-2 image of its SU(2) element (spin_rotation)
+  // (2) spin rotation exp(-iK) b, K = c1 d F.f, applied as an increment.
+  //     FP32, when every point of the warp has |K| = 2 |c1 d| |F| <= 3.5e-3:
+  //     the degree-2 Taylor polynomial, e = -iK (b - (i/2) K b); its
+  //     remainder |K|^3/6 < 7.2e-9 relative is a quarter of an FP32
+  //     rounding and it changes |b|^2 by |K|^4/4 < 4e-11.  Otherwise the
+  //     spin-2 image of the SU(2) element (spin_rotation), exact for any K.
+  bool taylor = false;
+  if constexpr (F32) {
+    const R k1 = c1 * delta;
+    const R K2 = (R)4 * k1 * k1 * (cabs2(Fp) + Fz * Fz);
+    taylor = __all_sync(0xffffffffu, K2 <= (R)(3.5e-3 * 3.5e-3));
+    if (taylor) {
+      C Kb[5], cb[5], e[5];
+      spin_dot<R>(k1 * Fz, cscale(Fp, k1), b, Kb);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) cb[k] = caxpy(b[k], cmulmi(Kb[k]), (R)0.5);
+      spin_dot<R>(k1 * Fz, cscale(Fp, k1), cb, e);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        e[k] = cmulmi(e[k]);
+        inc[k] = cadd(inc[k], e[k]);
+        b[k] = cadd(b[k], e[k]);
+      }
+    }
+  }
   SpinRot<R> sr;
-  if (spin_rotation<R>(Fz, Fp, c1, delta, sr)) {
+  if (!taylor && spin_rotation<R>(Fz, Fp, c1, delta, sr)) {
     const C am1 = sr.am1, bhat = sr.bhat;
     const R cpm1 = sr.cpm1, sp = sr.sp;
     C e[5];
@@ -323,7 +395,8 @@ __device__ __forceinline__ void nonlinear_point(cplx<R> (&v)[5], R V, R delta,
       b[k] = cadd(b[k], e[k]);
     }
   }
-  // (3) scalar phase exp(-i d (V + (c0 + c2/5) rho)) - 1 = (-2 sin^2(ph/2), -sin(ph))
+  // (3) scalar phase exp(-i ph) - 1 = (-2 sin^2(ph/2), -sin ph), ph = d (V + (c0 + c2/5) rho),
+  //     from the half angle so that |1 + pm1|^2 - 1 = -4 sh^2 (1 - sh^2 - ch^2)
   R sh3, ch3;
   sincos_small((R)-0.5 * delta * (V + c0p * rho), &sh3, &ch3);
   const C pm1 = mkc((R)-2 * sh3 * sh3, (R)2 * sh3 * ch3);
@@ -367,13 +440,25 @@ struct XCfg {
 // stages, processes and reads back only the points it holds, so the rows
 // of a CTA synchronise independently (Cfg::GT) and the nonlinear flow needs
 // one barrier.
-template <typename R, int N, int E, int G>
-__global__ void __launch_bounds__(XCfg<R, N, E, G>::THREADS, XCfg<R, N, E, G>::MINB)
-k_xpass(XPassArgs<R> a) {
+// Field loads of a pass: plain (may be served by L1), or L2-only when the
+// data was written by other CTAs of the same launch (the persistent
+// ensemble kernel), whose stores the SM's L1 does not see.
+template <bool CG, typename C>
+__device__ __forceinline__ C ld_field(const C* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// Body of the x-pass for block (bx, member): the CTA's rows are
+// bx * ROWS .. bx * ROWS + ROWS - 1 of member `member`.  Called by k_xpass
+// with the block's own coordinates and by the persistent ensemble kernel
+// for each work item it takes.
+template <typename R, int N, int E, int G, bool CG = false>
+__device__ __forceinline__ void xpass_body(const XPassArgs<R>& a, int bx, int member,
+                                           unsigned char* smem_raw) {
   typedef cplx<R> C;
   typedef XCfg<R, N, E, G> Cfg;
   constexpr int T = Cfg::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
   C* xb = reinterpret_cast<C*>(tw + N);
   // rotation cos/sin and the member's parameters in R, formed once per CTA
@@ -384,7 +469,7 @@ k_xpass(XPassArgs<R> a) {
   const int i = threadIdx.x - g * T;
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
   if ((a.mode & XP_NL) && threadIdx.x == 0) {
-    const MemberPrm& P = a.mp[blockIdx.y];
+    const MemberPrm& P = a.mp[member];
     const double t = *a.t_base + a.t_off;
     double sn, cs;
     sincos(P.omega * t, &sn, &cs);
@@ -398,19 +483,19 @@ k_xpass(XPassArgs<R> a) {
     s_prm[7] = (R)P.gz2h;
   }
   if ((a.mode & XP_NL) && threadIdx.x < Cfg::ROWS) {
-    const int rr = blockIdx.x * Cfg::ROWS + threadIdx.x;
+    const int rr = bx * Cfg::ROWS + threadIdx.x;
     s_yz[threadIdx.x][0] = a.y0 + (R)(rr % a.ny) * a.hy;
     s_yz[threadIdx.x][1] = a.z0 + (R)(rr / a.ny) * a.hz;
   }
-  const int row = blockIdx.x * Cfg::ROWS + g;
+  const int row = bx * Cfg::ROWS + g;
   const bool valid = row < a.rows;
-  C* base = a.field + (size_t)blockIdx.y * 5 * a.ntot + (size_t)(valid ? row : 0) * N + i;
+  C* base = a.field + (size_t)member * 5 * a.ntot + (size_t)(valid ? row : 0) * N + i;
   C v[5][E];
 #pragma unroll
   for (int c = 0; c < 5; ++c)
 #pragma unroll
     for (int e = 0; e < E; ++e)
-      v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
+      v[c][e] = valid ? ld_field<CG>(base + (size_t)c * a.ntot + T * e) : mkc((R)0, (R)0);
   // twiddles, s_prm and s_yz come from other rows' threads
   __syncthreads();
   constexpr int GT = Cfg::GT;
@@ -454,6 +539,13 @@ k_xpass(XPassArgs<R> a) {
 #pragma unroll
       for (int e = 0; e < E; ++e) base[(size_t)c * a.ntot + T * e] = v[c][e];
   }
+}
+
+template <typename R, int N, int E, int G>
+__global__ void __launch_bounds__(XCfg<R, N, E, G>::THREADS, XCfg<R, N, E, G>::MINB)
+k_xpass(XPassArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  xpass_body<R, N, E, G>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ----------------------------------------------------------------------------
@@ -539,28 +631,40 @@ __device__ __forceinline__ void mix_entry(cplx<R> (&v)[5], const LPassArgs<R>& a
   const C bhat = mkc(ps < 0 ? -m.bx : m.bx, qs < 0 ? m.by : -m.by);
   C e[5];
   spin2_increment<R>(v, mkc(m.am1r, m.am1i), bhat, m.cm1, m.sp, e);
+  C t[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const C x = cadd(v[k], e[k]);
-    const C t = cadd(v[k], cadd(e[k], cmul(kh, x)));
-    v[k] = mkc(mulc2(t.x, a.inv_hi, a.inv_lo), mulc2(t.y, a.inv_hi, a.inv_lo));
+    t[k] = cadd(v[k], cadd(e[k], cmul(kh, x)));
+  }
+  if (a.inv_lo == (R)0) {
+    // 1/N exact (N a power of two): one packed scaling
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = cscale(t[k], a.inv_hi);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      v[k] = mkc(mulc2(t[k].x, a.inv_hi, a.inv_lo), mulc2(t[k].y, a.inv_hi, a.inv_lo));
   }
 }
 
-template <typename R, int N, int E, int G>
-__global__ void __launch_bounds__(LCfg<R, N, E, G>::THREADS, LCfg<R, N, E, G>::MINB)
-k_linepass(LPassArgs<R> a) {
+// Body of the line pass for block (bx, plane, member): the CTA's columns
+// are bx * TILE .. bx * TILE + TILE - 1 of plane `plane` (the z slice for
+// y-lines, the y row for z-lines) of member `member`.  Called by k_linepass
+// with the block's own coordinates and by the persistent ensemble kernel.
+template <typename R, int N, int E, int G, bool CG = false>
+__device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int plane, int member,
+                                              unsigned char* smem_raw) {
   typedef cplx<R> C;
   typedef LCfg<R, N, E, G> Cfg;
   constexpr int T = Cfg::T;
   constexpr int TILE = Cfg::TILE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
   C* xb = reinterpret_cast<C*>(tw + N);
   const int col = threadIdx.x % TILE;
   const int i = threadIdx.x / TILE;
   for (int k = threadIdx.x; k < N; k += Cfg::THREADS) tw[k] = a.tw[k];
-  const int xcol = blockIdx.x * TILE + col;
+  const int xcol = bx * TILE + col;
   const bool valid = xcol < a.nx;
   // With the mix, the mode-table entries the tile uses go to shared memory
   // behind the exchange buffers by asynchronous copies issued here, which
@@ -568,7 +672,7 @@ k_linepass(LPassArgs<R> a) {
   // launch adds the bytes of line_table_bytes for exactly these cases):
   //   2D y-lines: the rows |p| of the tile's columns (idle columns of a
   //     ragged tile use p = 0), TILE x (N/2 + 1) entries;
-  //   3D z-lines: the tile's TILE entries at (|p|, |q|), q = blockIdx.y,
+  //   3D z-lines: the tile's TILE entries at (|p|, |q|), q = plane,
   //     then the z factors kz[0..N).
   constexpr int HN = N / 2 + 1;
   constexpr int GR = MT_STRIDE * (int)sizeof(R) / 16;          // 16-byte pieces per entry
@@ -576,15 +680,15 @@ k_linepass(LPassArgs<R> a) {
   const bool stab = (a.mode & LP_MIX) && a.axis == 1;
   const bool stabz = (a.mode & LP_MIX) && a.axis == 2;
   if (stabz) {
-    const R* mtm = a.mt + (size_t)blockIdx.z * a.mt_member;
-    const int qq = blockIdx.y;
+    const R* mtm = a.mt + (size_t)member * a.mt_member;
+    const int qq = plane;
     int aqs = qq < a.NY / 2 ? qq : qq - a.NY;
     aqs = aqs < 0 ? -aqs : aqs;
     constexpr int KZ = N * (int)sizeof(C) / 16;
     for (int k = threadIdx.x; k < TILE * GR + KZ; k += Cfg::THREADS) {
       if (k < TILE * GR) {
         const int cc = k / GR, g = k - cc * GR;
-        int p = blockIdx.x * TILE + cc;
+        int p = bx * TILE + cc;
         p = p < a.nx ? p : 0;
         int ps = p < a.NX / 2 ? p : p - a.NX;
         ps = ps < 0 ? -ps : ps;
@@ -600,11 +704,11 @@ k_linepass(LPassArgs<R> a) {
     cp_async_commit();
   }
   if (stab) {
-    const R* mtm = a.mt + (size_t)blockIdx.z * a.mt_member;
+    const R* mtm = a.mt + (size_t)member * a.mt_member;
     for (int k = threadIdx.x; k < TILE * HN * GR; k += Cfg::THREADS) {
       const int cc = k / (HN * GR);
       const int rem = k - cc * HN * GR;
-      int p = blockIdx.x * TILE + cc;
+      int p = bx * TILE + cc;
       p = p < a.nx ? p : 0;
       int ps = p < a.NX / 2 ? p : p - a.NX;
       ps = ps < 0 ? -ps : ps;
@@ -613,7 +717,7 @@ k_linepass(LPassArgs<R> a) {
     }
     cp_async_commit();
   }
-  C* base = a.field + (size_t)blockIdx.z * 5 * a.ntot + (size_t)blockIdx.y * a.plane_stride +
+  C* base = a.field + (size_t)member * 5 * a.ntot + (size_t)plane * a.plane_stride +
             (valid ? xcol : 0) + (size_t)i * a.line_stride;
   const size_t step = (size_t)T * a.line_stride;
   C v[5][E];
@@ -621,7 +725,7 @@ k_linepass(LPassArgs<R> a) {
   for (int c = 0; c < 5; ++c)
 #pragma unroll
     for (int e = 0; e < E; ++e)
-      v[c][e] = valid ? base[(size_t)c * a.ntot + e * step] : mkc((R)0, (R)0);
+      v[c][e] = valid ? ld_field<CG>(base + (size_t)c * a.ntot + e * step) : mkc((R)0, (R)0);
   C* b0 = xb + col * Cfg::LP;
   const int bstride = TILE * Cfg::LP;
   if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
@@ -646,7 +750,7 @@ k_linepass(LPassArgs<R> a) {
       cp_async_wait();
       __syncthreads();
       const int ps = pm < a.NX / 2 ? pm : pm - a.NX;
-      const int qq = blockIdx.y;
+      const int qq = plane;
       const int qs = qq < a.NY / 2 ? qq : qq - a.NY;
       const ModeEntry<R> m = load_mode_shared(smt, col);
       const C kh = mkc(m.khr, m.khi);
@@ -668,6 +772,13 @@ k_linepass(LPassArgs<R> a) {
 #pragma unroll
       for (int e = 0; e < E; ++e) base[(size_t)c * a.ntot + e * step] = v[c][e];
   }
+}
+
+template <typename R, int N, int E, int G>
+__global__ void __launch_bounds__(LCfg<R, N, E, G>::THREADS, LCfg<R, N, E, G>::MINB)
+k_linepass(LPassArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  linepass_body<R, N, E, G>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ----------------------------------------------------------------------------

@@ -116,6 +116,10 @@ def lib():
         "sgp_get_plan": (I, [P, ctypes.POINTER(ctypes.c_int)]),
         "sgp_autotune": (I, [P, I, I, ctypes.POINTER(ctypes.c_double)]),
         "sgp_ensemble_autotune": (I, [P, I, I]),
+        "sgp_ensemble_set_persistent": (I, [P, I]),
+        "sgp_ensemble_persistent": (I, [P]),
+        "sgp_ensemble_set_wait_limit": (I, [P, D]),
+        "sgp_ensemble_inject_stall": (I, [P, I]),
         "sgp_record": (I, [P, LL, D, I, LL]),
         "sgp_backward": (I, [P, P, I, P, I, ctypes.POINTER(ctypes.c_double)]),
         "sgp_set_profiling": (I, [P, I]),
@@ -591,6 +595,23 @@ class Ensemble:
     def autotune(self, reps=20, force=False):
         _echeck(lib().sgp_ensemble_autotune(self.handle, int(reps), SGP_TUNE_FORCE if force else 0),
                 self.handle)
+
+    def set_persistent(self, enable):
+        """sgp_ensemble_set_persistent: run the steps in the persistent
+        work-queue kernel (default when the ensemble qualifies) or not."""
+        _echeck(lib().sgp_ensemble_set_persistent(self.handle, int(bool(enable))), self.handle)
+
+    @property
+    def persistent(self):
+        return bool(lib().sgp_ensemble_persistent(self.handle))
+
+    def set_wait_limit(self, seconds):
+        _echeck(lib().sgp_ensemble_set_wait_limit(self.handle, float(seconds)), self.handle)
+
+    def inject_stall(self, member):
+        """Test hook: the next step's first work item of `member` does not
+        signal its completion (sgp_ensemble_inject_stall)."""
+        _echeck(lib().sgp_ensemble_inject_stall(self.handle, int(member)), self.handle)
 
     def observables(self):
         arr = (Obs * self.count)()

@@ -1,9 +1,13 @@
 """GPU parity of the adjoint (sgp_record / sgp_backward and the autograd
-Function) against the FP64 oracle gradient and central finite differences.
+Function) against the two FP64 oracle gradients (the tangent-linear one of
+oracle/sgp_tangent.py and the central differences of oracle/sgp_grad.py)
+and GPU central finite differences.
 
 Objective: the terminal density misfit J of oracle/sgp_grad.py.  Gradient
 convention dJ/dRe + i dJ/dIm; parameter slots (Omega, gamma, c0, c1, c2).
 Tolerances:
+  * FP64 GPU adjoint vs the tangent-linear oracle gradient: 1e-8 relative
+    (both exact up to FP64 rounding);
   * FP64 GPU adjoint vs oracle central FD: 1e-6 relative (the FD truncation
     error of the pinned oracle gradient is about 1e-8 relative at these
     steps; the adjoint itself is exact up to rounding);
@@ -24,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import sgp_grad as G
 from oracle import sgp_oracle as O
+from oracle import sgp_tangent as TL
 from paper_2603_25282_gb300 import inputs, sgp
 from paper_2603_25282_gb300.autograd import density_misfit, propagate
 
@@ -87,6 +92,45 @@ def test_adjoint_fp64_matches_oracle_fd(scheme, nsteps, interval):
     scale = max(abs(v) for v in fd_par.values())
     for k, name in enumerate(NAMES):
         assert abs(dp[k] - fd_par[name]) <= 1e-6 * scale, (name, dp[k], fd_par[name])
+
+
+@pytest.mark.parametrize("scheme,nsteps,interval", [("ts2", 6, 0), ("ts4", 4, 3), ("ts2_lnl", 5, 2),
+                                                     ("ts4_l", 4, 1)])
+def test_adjoint_fp64_matches_tangent_oracle(scheme, nsteps, interval):
+    """The adjoint (reverse sweep over the checkpointed run) against the
+    forward-mode dual-number gradient of the oracle: three state directions
+    and all five parameters to 1e-8."""
+    n, L, dt = (16, 16), 8.0, 2e-3
+    psi0 = inputs.gaussian_random_phase(n, L, seed=14, amp=0.3)
+    c, w = inputs.density_target(n, L, seed=15)
+    g0, dp = _run_adjoint(n, L, PRM_SMALL, psi0, dt, nsteps, scheme, "f64", c, w, interval)
+    grid = O.Grid(n, L)
+    rng = np.random.default_rng(16)
+    dirs = [rng.standard_normal(psi0.shape) + 1j * rng.standard_normal(psi0.shape) for _ in range(3)]
+    tl_dirs, tl_par = TL.gradient_tangent(psi0, grid, PRM_SMALL, dt, nsteps, scheme, c, w,
+                                          directions=dirs, params=NAMES)
+    for V, ref in zip(dirs, tl_dirs):
+        got = float(np.real(np.vdot(g0, V)))
+        assert abs(got - ref) <= 1e-8 * abs(ref), (got, ref)
+    scale = max(abs(v) for v in tl_par.values())
+    for k, name in enumerate(NAMES):
+        assert abs(dp[k] - tl_par[name]) <= 1e-8 * scale, (name, dp[k], tl_par[name])
+
+
+def test_adjoint_fp64_3d_matches_tangent_oracle():
+    n, L, dt, nsteps = (16, 16, 16), 6.0, 2e-3, 3
+    prm = dataclasses.replace(PRM_SMALL, gz=1.7)
+    psi0 = inputs.gaussian_random_phase(n, L, seed=24, amp=0.3)
+    c, w = inputs.density_target(n, L, seed=25)
+    g0, dp = _run_adjoint(n, L, prm, psi0, dt, nsteps, "ts4", "f64", c, w)
+    V = np.random.default_rng(26).standard_normal(psi0.shape) * (1 + 1j)
+    tl_dirs, tl_par = TL.gradient_tangent(psi0, O.Grid(n, L), prm, dt, nsteps, "ts4", c, w,
+                                          directions=[V], params=NAMES)
+    got = float(np.real(np.vdot(g0, V)))
+    assert abs(got - tl_dirs[0]) <= 1e-8 * abs(tl_dirs[0])
+    scale = max(abs(v) for v in tl_par.values())
+    for k, name in enumerate(NAMES):
+        assert abs(dp[k] - tl_par[name]) <= 1e-8 * scale, name
 
 
 def test_adjoint_fp64_3d_matches_oracle_fd():

@@ -1,14 +1,17 @@
 """Table 2 (Sec. 4.1, Example 1, 3D case) reproduced on the GPU FP64 path:
 the temporal errors of TS2 and TS4 at t = 0.3 for tau = 1/40 .. 1/320, all
 five components, against the printed values (tests/golden/
-table2_3d_temporal.txt), and the convergence rates 2 and 4.
+table2_3d_temporal.txt), and the convergence rates 2 and 4; once at
+h = 1/8 (fast) and once at the paper's own h0 = 1/16 (N = 256, a 1.3 GB
+FP64 field).
 
 Set-up as printed: [-8, 8]^3, c0 = 10, c1 = -1, c2 = 1, Omega = 0.2,
 gamma = 0.1, initial data (ini1), unit isotropic trap.  Differences from the
 paper's run, chosen so the test takes seconds: h = 1/8 (N = 128) instead of
 h0 = 1/16 (the printed spatial error at h = 1/8 is 5e-13, below every
 temporal entry), and a TS4 reference at tau0 = 1/2560 instead of 1e-4 (its
-own error is 4096 times below the tau = 1/320 entry).
+own error is 4096 times below the tau = 1/320 entry).  At h0 = 1/16 the
+reference is TS4 at tau0 = 1/1280 (256 times below the tau = 1/320 entry).
 """
 import os
 
@@ -33,8 +36,8 @@ def _golden():
     return rows
 
 
-def _run(psi0, scheme, tau_inv):
-    c = sgp.Context((N, N, N), L, prec="f64")
+def _run(psi0, scheme, tau_inv, n=N):
+    c = sgp.Context((n, n, n), L, prec="f64")
     c.set_params(**PRM)
     c.set_state(psi0[None].copy(), 0.0)
     steps = int(round(T * tau_inv))
@@ -69,3 +72,27 @@ def test_table2_convergence_rates(runs):
             for k in range(5):
                 rate = np.log2(runs[(sch, a)][k] / runs[(sch, b)][k])
                 assert abs(rate - p) < 0.04, (sch, a, k, rate)
+
+
+@pytest.fixture(scope="module")
+def runs_h0():
+    n = 256
+    psi0 = inputs.ini_example1((n, n, n), L)
+    ref = _run(psi0, "ts4", 1280, n)
+    out = {}
+    for sch in ("ts2", "ts4"):
+        for ti in (40, 80, 160, 320):
+            r = _run(psi0, sch, ti, n)
+            out[(sch, ti)] = [np.linalg.norm(ref[k] - r[k]) / np.linalg.norm(ref[k]) for k in range(5)]
+    return out
+
+
+def test_table2_temporal_errors_at_paper_h0(runs_h0):
+    gold = _golden()
+    for key, errs in runs_h0.items():
+        for e, pe in zip(errs, gold[key]):
+            assert abs(e / pe - 1) < 5e-3, (key, errs, gold[key])
+    for sch, p in (("ts2", 2.0), ("ts4", 4.0)):
+        for a, b in ((40, 80), (80, 160), (160, 320)):
+            for k in range(5):
+                assert abs(np.log2(runs_h0[(sch, a)][k] / runs_h0[(sch, b)][k]) - p) < 0.04

@@ -9,7 +9,9 @@ fixed-size device arrays inside the library, shared by every call, so the
 test makes calls in a row with different shapes and precisions: what one
 call leaves in the scratch must not leak into the next.
 
-This file is named to be collected last.
+The test holds on its own: it passes alone in a fresh process and after
+the other tests (the first call on the device is the entry point's set-up,
+made inside the test).  The file name puts it last in a run.
 """
 import numpy as np
 import pytest
@@ -30,14 +32,9 @@ def _reference(n, L, batch, prec, fields, t):
         return c.observables()
 
 
-def _static(n, L, batch, prec, fields, t):
-    import torch
-    dev = torch.from_numpy(np.ascontiguousarray(fields)).to("cuda:0")
-    torch.cuda.synchronize()
-    out = sgp.observables_static(n, L, dev.data_ptr(), batch=batch, prec=prec, t=t,
-                                 device=0, stream=None, **PRM)
-    del dev
-    return out
+def _static(n, L, batch, prec, dev, t):
+    return sgp.observables_static(n, L, dev.data_ptr(), batch=batch, prec=prec, t=t,
+                                  device=0, stream=None, **PRM)
 
 
 def _fields(n, L, batch, prec, seed):
@@ -58,21 +55,36 @@ def _check(got, ref):
             assert abs(a - b) < 1e-10 * max(1.0, abs(b))
 
 
-def test_static_observables_match_context_on_calls_in_a_row():
-    pytest.importorskip("torch")
+def test_static_observables_match_context_and_allocate_nothing():
+    """Calls in a row, with different shapes and precisions, each made twice,
+    match the context observables; after the first call on the device (the
+    set-up, which loads the kernels and the fixed scratch) the device's free
+    memory does not change across the calls, and sgp_last_error(NULL) is
+    empty after each successful call."""
+    torch = pytest.importorskip("torch")
     cases = [
         ((64, 64), 8.0, 2, "f64", 0.7),
         ((48, 96), (6.0, 9.0), 1, "f32", 0.3),
         ((16, 32, 16), (4.0, 5.0, 4.0), 3, "f64", 0.2),
+        ((128, 128), 8.0, 4, "f32", 0.5),
         ((64, 64), 8.0, 2, "f64", 0.7),
     ]
+    # references through contexts, and every device field, before measuring
+    refs, devs = [], []
     for i, (n, L, batch, prec, t) in enumerate(cases):
         f = _fields(n, L, batch, prec, seed=40 + 10 * i)
-        ref = _reference(n, L, batch, prec, f, t)
-        first = _static(n, L, batch, prec, f, t)
-        second = _static(n, L, batch, prec, f, t)
-        _check(first, ref)
-        _check(second, ref)
+        refs.append(_reference(n, L, batch, prec, f, t))
+        devs.append(torch.from_numpy(np.ascontiguousarray(f)).to("cuda:0"))
+    torch.cuda.synchronize()
+    n, L, batch, prec, t = cases[0]
+    _check(_static(n, L, batch, prec, devs[0], t), refs[0])      # set-up call
+    free0 = torch.cuda.mem_get_info(0)[0]
+    for (n, L, batch, prec, t), dev, ref in zip(cases, devs, refs):
+        for _ in range(2):
+            _check(_static(n, L, batch, prec, dev, t), ref)
+            assert sgp.lib().sgp_last_error(None).decode() == ""
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(0)[0] == free0
 
 
 def test_static_observables_reject_oversized_requests():
