@@ -537,7 +537,9 @@ def run_ours(args, rank, world, local_rank):
                        "plan": plan, "tune_ms": tune_ms},
             "gpu_launches": launches,
             "clocks": clocks,
-            "roofline": dict(roof, kernels={k: {"launches": v[0], "ms": v[1]}
+            "roofline": dict(roof, kernels={k: {"launches": v[0], "ms": v[1], "avg_launch_ms": v[1] / v[0],
+                                                "hbm_frac": per_pass_bytes / (v[1] / v[0] * 1e-3) / 1e9 / hbm_peak
+                                                if k in ("xpass", "linepass_y", "linepass_z") else None}
                                             for k, v in prof.items() if v[0]}),
             "step_hbm": {"algorithmic_bytes_per_point_step": bpp, "achieved_gbs": step_gbs,
                          "frac": step_gbs / hbm_peak,
