@@ -490,7 +490,7 @@ def run_ours(args, rank, world, local_rank):
     pinned = torch.from_numpy(host).pin_memory()
     out_pinned = torch.empty_like(pinned).pin_memory()
     e2e_steps = max(1, min(args.steps, 8))
-    chunks = min(batch, 8)
+    chunks = min(batch, 16)
     ctx.step_host(pinned, 0.0, 1, dt, scheme, chunks=chunks, out=out_pinned)
     barrier()
     t0 = time.perf_counter()
