@@ -415,8 +415,12 @@ sgp_status sgp_ensemble_inject_stall(sgp_ens* ens, int member);
  * 5*nz*ny*nx elements; host_in[m] may equal host_out[m]).  The same result
  * as count sgp_ensemble_set_member_state calls, sgp_ensemble_step and count
  * sgp_ensemble_get_member_state calls, with the copies issued
- * asynchronously in stream order and a single synchronisation at the end
- * (page-locked buffers let the copies run at full speed).  Returns when
+ * asynchronously in stream order and a single synchronisation at the end.
+ * When every buffer is page-locked and mapped into the device's address
+ * space (cudaHostAlloc, or cudaHostRegister with mapping) and 16-byte
+ * aligned, all copies of one direction are a single kernel launch that
+ * reads or writes the host buffers through that mapping (two launches per
+ * call); otherwise one copy per member and direction.  Returns when
  * every host_out[m] holds its result.  Errors: SGP_EINVAL for NULL arrays
  * or buffers, non-finite t0, nsteps < 0, dt <= 0, an unknown scheme;
  * SGP_ECUDA for a failed copy or launch. */

@@ -181,6 +181,49 @@ __global__ void k_linear_tables(double delta, const MemberPrm* mp, int NX, int N
 __global__ void k_set_time(double* t, double v) { *t = v; }
 __global__ void k_add_time(double* t, double v) { *t += v; }
 
+// Copies of many separate buffers in one launch: the ensemble's member
+// states between the caller's page-locked host buffers (read and written by
+// the GPU through their device mapping) and the member fields.  Entry m
+// moves n16 16-byte units from src to dst; its blocks start at block
+// `first` (kXferChunk units per block, the last one partial).
+struct MemberXfer {
+  const uint4* src;
+  uint4* dst;
+  long long n16;
+  long long first;
+};
+constexpr int kXferThreads = 256;
+constexpr int kXferUnroll = 16;
+constexpr int kXferChunk = kXferThreads * kXferUnroll;
+
+__global__ void __launch_bounds__(kXferThreads) k_copy_members(const MemberXfer* __restrict__ x, int count) {
+  __shared__ int s_m;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = count - 1;                 // the last entry whose first block <= blockIdx.x
+    const long long b = blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (x[mid].first <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    s_m = lo;
+  }
+  __syncthreads();
+  const MemberXfer m = x[s_m];
+  const long long base = (blockIdx.x - m.first) * (long long)kXferChunk + threadIdx.x;
+  uint4 v[kXferUnroll];
+#pragma unroll
+  for (int k = 0; k < kXferUnroll; ++k) {
+    const long long j = base + (long long)k * kXferThreads;
+    if (j < m.n16) v[k] = m.src[j];
+  }
+#pragma unroll
+  for (int k = 0; k < kXferUnroll; ++k) {
+    const long long j = base + (long long)k * kXferThreads;
+    if (j < m.n16) m.dst[j] = v[k];
+  }
+}
+
 struct LinTables {
   double delta = 0.0;
   void* mt = nullptr;    // per-mode tables, MT_STRIDE values per (|p|, |q|), per member
@@ -1985,6 +2028,9 @@ struct sgp_ens {
   };
   std::vector<PProg> progs;
   int stall_member = -1;            // test hook: withhold one completion signal
+  // sgp_ensemble_step_host with page-locked buffers: the copy lists of
+  // k_copy_members (in, then out) on the device
+  MemberXfer* xfer_dev = nullptr;
 };
 
 namespace {
@@ -2492,13 +2538,56 @@ sgp_status sgp_ensemble_step_host(sgp_ens* e, const void* const* host_in, double
   if (!valid_scheme(scheme)) return efail(e, SGP_EINVAL, "unknown scheme %d", scheme);
   DeviceGuard guard(e->device);
   // every copy in, the steps and every copy out in the order of the
-  // ensemble stream, one synchronisation at the end
+  // ensemble stream, one synchronisation at the end.  When every buffer is
+  // page-locked and mapped into the device (cudaHostAlloc, or registered),
+  // each direction is one k_copy_members launch; otherwise one copy per
+  // member and direction.
+  std::vector<MemberXfer> xl;
+  long long blocks[2] = {0, 0};
+  for (int dir = 0; dir < 2; ++dir)
+    for (int m = 0; m < e->count; ++m) {
+      sgp_ctx* c = e->groups[e->member_group[m]];
+      const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+      const void* h = dir == 0 ? host_in[m] : host_out[m];
+      cudaPointerAttributes pa{};
+      if (bytes % 16 != 0 || cudaPointerGetAttributes(&pa, h) != cudaSuccess ||
+          pa.type != cudaMemoryTypeHost || !pa.devicePointer ||
+          reinterpret_cast<uintptr_t>(pa.devicePointer) % 16 != 0) {
+        cudaGetLastError();          // an unregistered pointer may leave an error behind
+        xl.clear();
+        dir = 2;
+        break;
+      }
+      char* f = (char*)c->field + (size_t)e->member_index[m] * bytes;
+      MemberXfer x;
+      x.src = (const uint4*)(dir == 0 ? pa.devicePointer : (void*)f);
+      x.dst = (uint4*)(dir == 0 ? (void*)f : pa.devicePointer);
+      x.n16 = (long long)(bytes / 16);
+      x.first = blocks[dir];
+      blocks[dir] += (x.n16 + kXferChunk - 1) / kXferChunk;
+      xl.push_back(x);
+    }
+  const bool kcopy = !xl.empty() && blocks[0] < (1LL << 31) && blocks[1] < (1LL << 31);
   cudaError_t ce = cudaSuccess;
-  for (int m = 0; m < e->count && ce == cudaSuccess; ++m) {
-    sgp_ctx* c = e->groups[e->member_group[m]];
-    const size_t bytes = 5 * (size_t)c->ntot * c->elem;
-    ce = cudaMemcpyAsync((char*)c->field + (size_t)e->member_index[m] * bytes, host_in[m], bytes,
-                         cudaMemcpyHostToDevice, e->stream);
+  if (kcopy) {
+    if (!e->xfer_dev)
+      ce = dev_alloc(e->groups[0], (void**)&e->xfer_dev, 2 * sizeof(MemberXfer) * (size_t)e->count);
+    // pageable source: staged before the call returns, in stream order
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(e->xfer_dev, xl.data(), xl.size() * sizeof(MemberXfer), cudaMemcpyHostToDevice,
+                           e->stream);
+    if (ce == cudaSuccess) {
+      k_copy_members<<<(unsigned)blocks[0], kXferThreads, 0, e->stream>>>(e->xfer_dev, e->count);
+      ce = cudaGetLastError();
+      e->launches++;
+    }
+  } else {
+    for (int m = 0; m < e->count && ce == cudaSuccess; ++m) {
+      sgp_ctx* c = e->groups[e->member_group[m]];
+      const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+      ce = cudaMemcpyAsync((char*)c->field + (size_t)e->member_index[m] * bytes, host_in[m], bytes,
+                           cudaMemcpyHostToDevice, e->stream);
+    }
   }
   if (ce != cudaSuccess) {
     cudaStreamSynchronize(e->stream);
@@ -2514,11 +2603,19 @@ sgp_status sgp_ensemble_step_host(sgp_ens* e, const void* const* host_in, double
   if (nsteps > 0)
     st = e->prec == SGP_F32 ? ens_run<float>(e, nsteps, dt, scheme)
                             : ens_run<double>(e, nsteps, dt, scheme);
-  for (int m = 0; m < e->count && st == SGP_OK && ce == cudaSuccess; ++m) {
-    sgp_ctx* c = e->groups[e->member_group[m]];
-    const size_t bytes = 5 * (size_t)c->ntot * c->elem;
-    ce = cudaMemcpyAsync(host_out[m], (const char*)c->field + (size_t)e->member_index[m] * bytes,
-                         bytes, cudaMemcpyDeviceToHost, e->stream);
+  if (kcopy) {
+    if (st == SGP_OK) {
+      k_copy_members<<<(unsigned)blocks[1], kXferThreads, 0, e->stream>>>(e->xfer_dev + e->count, e->count);
+      ce = cudaGetLastError();
+      e->launches++;
+    }
+  } else {
+    for (int m = 0; m < e->count && st == SGP_OK && ce == cudaSuccess; ++m) {
+      sgp_ctx* c = e->groups[e->member_group[m]];
+      const size_t bytes = 5 * (size_t)c->ntot * c->elem;
+      ce = cudaMemcpyAsync(host_out[m], (const char*)c->field + (size_t)e->member_index[m] * bytes,
+                           bytes, cudaMemcpyDeviceToHost, e->stream);
+    }
   }
   const cudaError_t cs = cudaStreamSynchronize(e->stream);   // host buffers free after this
   if (st != SGP_OK) return st;
@@ -2595,6 +2692,7 @@ sgp_status sgp_ensemble_destroy(sgp_ens* e) {
     ens_free_progs(e);
     dev_free(e->groups[0], e->done_dev);
     dev_free(e->groups[0], e->ctl_dev);
+    dev_free(e->groups[0], e->xfer_dev);
   }
   for (sgp_ctx* c : e->groups) sgp_destroy(c);
   for (cudaStream_t s : e->gstreams) cudaStreamDestroy(s);

@@ -117,3 +117,50 @@ def test_ensemble_step_host_equals_member_calls():
             assert np.array_equal(inplace[k], ref[k])
         with pytest.raises(sgp.SgpError, match="EINVAL"):
             b.step_host(psis, float("inf"), 1, 1e-3)
+
+
+def test_ensemble_step_host_page_locked_copies_in_one_launch():
+    """Every buffer page-locked: each direction is one copy launch reading or
+    writing the host buffers through their device mapping (two launches more
+    than with pageable buffers); the results equal the per-member calls bit
+    for bit, also in place and with grids of the persistent kernel.  One
+    pageable buffer among them sends the call back to per-member copies."""
+    grids = [((64, 64), 8.0), ((128, 128), 8.0), ((96, 96), 8.0), ((64, 64), 8.0), ((256, 256), 8.0)]
+    plist = _plist(len(grids))
+    psis = [inputs.gaussian_random_phase(n, L, seed=90 + k, amp=0.3).astype(np.complex64)
+            for k, (n, L) in enumerate(grids)]
+    with sgp.Ensemble(grids, prec="f32") as a, sgp.Ensemble(grids, prec="f32") as b:
+        a.set_params(plist)
+        b.set_params(plist)
+        for k, p in enumerate(psis):
+            a.set_member_state(k, p.copy(), 0.1)
+        a.step(5, 1e-3, "ts2")
+        ref = [a.get_member_state(k) for k in range(len(grids))]
+        # pageable buffers: per-member copies
+        l0 = b.launch_count()
+        outs = b.step_host([p.copy() for p in psis], 0.1, 5, 1e-3, "ts2")
+        lp = b.launch_count() - l0
+        for k in range(len(grids)):
+            assert np.array_equal(outs[k], ref[k]), k
+        # page-locked in and out
+        srcs = [torch.from_numpy(p.copy()).pin_memory() for p in psis]
+        pouts = [torch.empty(p.shape, dtype=torch.complex64).pin_memory() for p in psis]
+        l0 = b.launch_count()
+        b.step_host(srcs, 0.1, 5, 1e-3, "ts2", outs=pouts)
+        assert b.launch_count() - l0 == lp + 2
+        for k in range(len(grids)):
+            assert np.array_equal(pouts[k].numpy(), ref[k]), k
+            assert np.array_equal(srcs[k].numpy(), psis[k])          # inputs untouched
+        # page-locked, in place
+        b.step_host(srcs, 0.1, 5, 1e-3, "ts2", outs=srcs)
+        for k in range(len(grids)):
+            assert np.array_equal(srcs[k].numpy(), ref[k]), k
+        # one pageable output among page-locked buffers
+        mixed = list(pouts)
+        mixed[2] = np.empty(psis[2].shape, dtype=np.complex64)
+        srcs = [torch.from_numpy(p.copy()).pin_memory() for p in psis]
+        l0 = b.launch_count()
+        b.step_host(srcs, 0.1, 5, 1e-3, "ts2", outs=mixed)
+        assert b.launch_count() - l0 == lp
+        assert np.array_equal(mixed[2], ref[2])
+        assert np.array_equal(mixed[4].numpy(), ref[4])
