@@ -304,7 +304,7 @@ struct sgp_ctx {
   size_t elem = 8;
   void* field = nullptr;
   void* tw[3] = {nullptr, nullptr, nullptr};     // twiddles of the default radix plan per axis
-  void* tw4[3] = {nullptr, nullptr, nullptr};    // FP32 radix-4 plan (variant 3), on demand
+  void* tw4[3] = {nullptr, nullptr, nullptr};    // FP32 plan of variant 3 (4 or 12 elements), on demand
   int var[3] = {0, 0, 0};                        // kernel variant per axis (x-pass, y, z lines)
   double* t_dev = nullptr;
   double t = 0.0;
@@ -1335,7 +1335,8 @@ sgp_status use_variant(sgp_ctx* c, int a, int v) {
   if (v == 3 && !c->tw4[a]) {
     SGP_CUDA(c, cudaStreamSynchronize(c->stream));
     SGP_CUDA(c, dev_alloc(c, &c->tw4[a], (size_t)c->n[a] * sizeof(TwE<float>)));
-    k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], 4, (TwE<float>*)c->tw4[a]);
+    k_twiddles_f32<<<(c->n[a] + 255) / 256, 256, 0, c->stream>>>(c->n[a], variant_elems_rt(4, c->n[a], 3),
+                                                                (TwE<float>*)c->tw4[a]);
     c->launches++;
     SGP_CUDA(c, cudaGetLastError());
   }

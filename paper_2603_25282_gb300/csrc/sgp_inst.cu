@@ -15,11 +15,7 @@
 #define SGP_VAR 0
 #endif
 
-#if SGP_VAR == 3
-#define SGP_FOR_EACH_VN SGP_FOR_EACH_N_POW2
-#else
 #define SGP_FOR_EACH_VN SGP_FOR_EACH_N
-#endif
 
 namespace sgp {
 
@@ -39,7 +35,6 @@ cudaError_t prepare(K kern, size_t smem, int* done_dev) {
 
 typedef SGP_REAL Real;
 constexpr int V = SGP_VAR;
-constexpr int G = variant_geom<V>();
 
 #if SGP_PART == 0
 
@@ -48,7 +43,7 @@ PassGeom xpass_geom_v<Real, V>(int N) {
   switch (N) {
 #define SGP_CASE(NN)                                                        \
   case NN: {                                                                \
-    typedef XCfg<Real, NN, variant_elems<Real, NN, V>(), G> Cfg;            \
+    typedef XCfg<Real, NN, variant_elems<Real, NN, V>(), variant_geom<NN, V, SGP_PART>()> Cfg;            \
     return PassGeom{Cfg::THREADS, Cfg::ROWS, Cfg::SMEM};                    \
   }
     SGP_FOR_EACH_VN(SGP_CASE)
@@ -61,6 +56,7 @@ PassGeom xpass_geom_v<Real, V>(int N) {
 template <int N>
 static cudaError_t xpass_prepare_n() {
   constexpr int E = variant_elems<Real, N, V>();
+  constexpr int G = variant_geom<N, V, SGP_PART>();
   static int done = -1;
   cudaError_t e = prepare(k_xpass<Real, N, E, G>, XCfg<Real, N, E, G>::SMEM, &done);
 #if SGP_VAR == 0
@@ -74,6 +70,7 @@ static cudaError_t xpass_prepare_n() {
 template <int N>
 static cudaError_t xpass_n(const XPassArgs<Real>& a, int members, cudaStream_t s) {
   constexpr int E = variant_elems<Real, N, V>();
+  constexpr int G = variant_geom<N, V, SGP_PART>();
   typedef XCfg<Real, N, E, G> Cfg;
   cudaError_t e = xpass_prepare_n<N>();
   if (e != cudaSuccess) return e;
@@ -141,7 +138,7 @@ PassGeom linepass_geom_v<Real, V>(int N) {
   switch (N) {
 #define SGP_CASE(NN)                                                        \
   case NN: {                                                                \
-    typedef LCfg<Real, NN, variant_elems<Real, NN, V>(), G> Cfg;            \
+    typedef LCfg<Real, NN, variant_elems<Real, NN, V>(), variant_geom<NN, V, SGP_PART>()> Cfg;            \
     return PassGeom{Cfg::THREADS, Cfg::TILE, Cfg::SMEM};                    \
   }
     SGP_FOR_EACH_VN(SGP_CASE)
@@ -154,6 +151,7 @@ PassGeom linepass_geom_v<Real, V>(int N) {
 template <int N>
 static cudaError_t linepass_prepare_n() {
   constexpr int E = variant_elems<Real, N, V>();
+  constexpr int G = variant_geom<N, V, SGP_PART>();
   static int done = -1;
   cudaError_t e = prepare(k_linepass<Real, N, E, G>,
                           LCfg<Real, N, E, G>::SMEM + LCfg<Real, N, E, G>::TAB, &done);
@@ -169,6 +167,7 @@ template <int N>
 static cudaError_t linepass_n(const LPassArgs<Real>& a, int planes, int members,
                               cudaStream_t s) {
   constexpr int E = variant_elems<Real, N, V>();
+  constexpr int G = variant_geom<N, V, SGP_PART>();
   typedef LCfg<Real, N, E, G> Cfg;
   cudaError_t e = linepass_prepare_n<N>();
   if (e != cudaSuccess) return e;

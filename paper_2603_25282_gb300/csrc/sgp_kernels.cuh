@@ -428,8 +428,8 @@ struct XCfg {
   // 128-thread geometry (at most 128 registers, a few spilled: 7% faster
   // than the natural ~160 registers at N = 128, 2% slower at N = 512,
   // where the autotuner prefers the 256-thread geometry anyway)
-  static constexpr int MINB = (sizeof(R) == 4 && G == 1 && 4 * SMEM <= 220 * 1024) ? 4
-                              : (2 * SMEM <= 220 * 1024) ? 2 : 1;
+  static constexpr int MINB = (sizeof(R) == 4 && G == 1 && E <= 8 && 4 * SMEM <= 220 * 1024) ? 4
+                              : (2 * SMEM <= 220 * 1024 && THREADS <= 128 * (E <= 8 ? 2 : 1)) ? 2 : 1;
 };
 
 // x-pass: rows of all five components.  The nonlinear flow runs on the rows
@@ -571,7 +571,7 @@ struct LCfg {
   // here: the larger buffers cost more than the barriers they save)
   static constexpr int NB = 2;
   static constexpr size_t SMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)(NB * TILE * LP);
-  static constexpr int MINB = (THREADS <= 256 && 2 * SMEM <= 220 * 1024) ? 2 : 1;
+  static constexpr int MINB = (THREADS <= (E <= 8 ? 256 : 128) && 2 * SMEM <= 220 * 1024) ? 2 : 1;
   // lines along y in 2D: the tile's slice of the per-mode table (TILE
   // columns x (N/2 + 1) entries), copied to shared memory asynchronously
   // at the start so that the mix does not wait on L2 for every mode

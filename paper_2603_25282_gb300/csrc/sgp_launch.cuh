@@ -36,28 +36,33 @@ inline bool supported_n(int n) {
 //      to 512 threads, TILE >= 4 FP32 / 2 FP64 columns) and radix plan
 //   1  CTAs of about half the threads (line pass: TILE down to 1)
 //   2  CTAs of about a quarter of the threads
-//   3  FP32, N a power of two: radix-4 plan (4 elements per thread instead
-//      of 8: more stages, half the registers per line element)
+//   3  FP32 only.  N a power of two: radix-4 plan (4 elements per thread
+//      instead of 8: more stages, half the registers per line element).
+//      N = 3*2^k: 12 elements per thread, radix 6 then 4s (96 = 6*4*4 in
+//      three stages instead of 6*2*2*2*2 in five), in CTAs of 128 threads
+//      (x-pass geometry 1, line-pass geometry 2: a thread holds 120
+//      registers of field data)
 constexpr int kVariants = 4;
 
 template <typename R, int N, int V>
 constexpr int variant_elems() {
-  return V == 3 ? 4 : elems_per_thread<R, N>();
+  return V == 3 ? (N % 3 == 0 ? 12 : 4) : elems_per_thread<R, N>();
 }
-template <int V>
+// geometry of variant V for the x-pass (PART 0) and the line pass (PART 1)
+template <int N, int V, int PART>
 constexpr int variant_geom() {
-  return V == 3 ? 0 : V;
+  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : V;
 }
 
 // Does variant V exist for line length N (prec_bytes 4 or 8)?
 inline bool variant_exists(int prec_bytes, int N, int V) {
   if (!supported_n(N) || V < 0 || V >= kVariants) return false;
-  if (V == 3) return prec_bytes == 4 && N % 3 != 0;
+  if (V == 3) return prec_bytes == 4;
   return true;
 }
 // Elements per thread of variant V (the twiddle table layout depends on it).
 inline int variant_elems_rt(int prec_bytes, int N, int V) {
-  if (V == 3) return 4;
+  if (V == 3) return N % 3 == 0 ? 12 : 4;
   return (N % 3 == 0) ? 6 : (prec_bytes == 4 ? 8 : 4);
 }
 

@@ -69,8 +69,12 @@ def test_every_variant_3d(prec, tol):
 def test_set_plan_rejects_missing_variant():
     c = sgp.Context((96, 64), 8.0, prec="f32")
     with pytest.raises(sgp.SgpError):
-        c.set_plan((3, 0))         # no radix-4 plan for N = 96
+        c.set_plan((sgp.N_VARIANTS, 0))      # no such variant
+    with pytest.raises(sgp.SgpError):
+        c.set_plan((0, -1))
     assert c.get_plan() == [0, 0, 0]
+    c.set_plan((3, 3))         # 12 elements per thread (N = 96), radix-4 plan (N = 64)
+    assert c.get_plan() == [3, 3, 0]
     c.close()
     c = sgp.Context((64, 64), 8.0, prec="f64")
     with pytest.raises(sgp.SgpError):
