@@ -812,10 +812,12 @@ def run_ens(args, rank, world, local_rank):
                                                           amp=0.01).astype(cdt)).pin_memory()
             for m in members]
     outs = [torch.empty_like(h).pin_memory() for h in host]
-    e2e_n = 4
+    e2e_n = 8
     tcur = 0.0                      # the ensemble clock, accumulated as the library does
     tcur += args.warmup * cfg["dt"]
     tcur += args.steps * cfg["dt"]
+    ens.step_host(host, tcur, 1, cfg["dt"], cfg["scheme"], outs=outs)      # untimed: builds the 1-step program
+    tcur += 1 * cfg["dt"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_n):            # one sgp_ensemble_step_host call per step
