@@ -1,6 +1,8 @@
 // sgp_api.cu -- the C ABI declared in include/sgp.h: contexts and ensembles,
 // per-substep tables, pass orchestration of TS2/TS4 (with CUDA-graph replay
 // of step chunks) and the observables.
+#include <cuda.h>
+#include <cudaTypedefs.h>   // the driver's tensor-map encoder, fetched through the runtime
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -305,6 +307,11 @@ struct sgp_ctx {
   void* field = nullptr;
   void* tw[3] = {nullptr, nullptr, nullptr};     // twiddles of the default radix plan per axis
   void* tw4[3] = {nullptr, nullptr, nullptr};    // FP32 plan of variant 3 (4 or 12 elements), on demand
+  // line-pass variant 4: tensor maps of the field per line axis (made on
+  // first use) and the word a tile-load wait that gave up sets
+  alignas(64) CUtensorMap tmap[3];
+  const void* tmap_field[3] = {nullptr, nullptr, nullptr};   // the field a map was made for
+  int* err_dev = nullptr;
   int var[3] = {0, 0, 0};                        // kernel variant per axis (x-pass, y, z lines)
   double* t_dev = nullptr;
   double t = 0.0;
@@ -530,6 +537,54 @@ void* window_field(sgp_ctx* c) {
   return (char*)c->field + (size_t)c->win0 * 5 * c->ntot * c->elem;
 }
 
+// The driver's cuTensorMapEncodeTiled, through the runtime (no link to the
+// driver library); null when the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of the FP32 field for the line pass along `axis` (variant 4):
+// 4D, [5 * batch][nz][ny][nx] of 8-byte elements, x innermost; the box is
+// TILE columns by tma_rows(N) line elements (y for axis 1, z for axis 2).
+// The map holds the field's address: it is made again when the field
+// buffer changes (the autotuner steps a scratch copy).
+sgp_status ensure_tmap(sgp_ctx* c, int axis) {
+  if (c->tmap_field[axis] == c->field) return SGP_OK;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(c, SGP_EUNSUPPORTED, "the driver has no tensor-map encoder (variant 4)");
+  const int N = c->n[axis];
+  const cuuint32_t tile = (cuuint32_t)linepass_geom<float>(N, 4).rows_or_tile;
+  int rows = 1;
+  for (int d = 1; d <= N; ++d)
+    if (N % d == 0 && N / d <= 256) {
+      rows = N / d;
+      break;
+    }
+  const cuuint64_t nx = (cuuint64_t)c->n[0], ny = (cuuint64_t)c->n[1], nz = (cuuint64_t)c->n[2];
+  const cuuint64_t dims[4] = {nx, ny, nz, (cuuint64_t)5 * c->batch};
+  const cuuint64_t strides[3] = {nx * 8, nx * ny * 8, nx * ny * nz * 8};
+  const cuuint32_t box[4] = {tile, axis == 1 ? (cuuint32_t)rows : 1u, axis == 2 ? (cuuint32_t)rows : 1u, 1u};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(&c->tmap[axis], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c->field, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, SGP_ECUDA, "tensor map for axis %d: driver error %d", axis, (int)r);
+  c->tmap_field[axis] = c->field;
+  return SGP_OK;
+}
+
 template <typename R>
 sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
   XPassArgs<R> a{};
@@ -606,6 +661,8 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
     a.inv_hi = (R)inv;
     a.inv_lo = (R)(inv - (double)a.inv_hi);
   }
+  a.mc0 = c->win0;
+  a.err = c->err_dev;
   if (c->rec) {
     // recorded for the persistent ensemble kernel (2D: lines along y)
     PersistPass<R> p{};
@@ -618,6 +675,15 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
     p.l = a;
     static_cast<std::vector<PersistPass<R>>*>(c->rec)->push_back(p);
     return SGP_OK;
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (c->var[axis] == 4) {
+      SGP_TRY(ensure_tmap(c, axis));
+      c->launches++;
+      ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
+      SGP_CUDA(c, launch_linepass_tma(c->n[axis], a, c->tmap[axis], planes, window_members(c), c->stream));
+      return SGP_OK;
+    }
   }
   c->launches++;
   ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
@@ -1372,7 +1438,7 @@ std::string tune_key(const sgp_ctx* c) {
 // warm-up step: the data stay a physical state, so the nonlinear flow takes
 // its usual branches, and the pass interplay of a real step is included.  A
 // variant replaces an earlier (lower-numbered) one only when it is at least
-// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][4]:
+// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][5]:
 // ms per step with that variant (-1 where a variant does not exist or the
 // axis is absent).
 template <typename R>
@@ -1396,6 +1462,7 @@ sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
     double best_ms = -1.0;
     for (int v = 0; v < kVariants && st == SGP_OK; ++v) {
       if (!variant_exists(pb, c->n[a], v)) continue;
+      if (a == 0 && v == 4) continue;     // the x-pass of variant 4 is variant 1
       st = use_variant(c, a, v);
       if (st != SGP_OK) break;
       c->launches++;
@@ -1663,6 +1730,10 @@ sgp_status sgp_create_grid(int dim, const int* n, const double* L, int batch, in
   }
   if ((e = dev_alloc(c, (void**)&c->t_dev, sizeof(double))) != cudaSuccess)
     return bail(SGP_ENOMEM, "time allocation", e);
+  if ((e = dev_alloc(c, (void**)&c->err_dev, sizeof(int))) != cudaSuccess)
+    return bail(SGP_ENOMEM, "error word allocation", e);
+  if ((e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream)) != cudaSuccess)
+    return bail(SGP_ECUDA, "error word clear", e);
   if ((e = dev_alloc(c, (void**)&c->mp_dev, sizeof(MemberPrm) * batch)) != cudaSuccess)
     return bail(SGP_ENOMEM, "parameter allocation", e);
   // observables scratch: the largest per-kernel partial array
@@ -1919,6 +1990,16 @@ sgp_status sgp_synchronize(sgp_ctx* c) {
   if (!c) return SGP_EINVAL;
   DeviceGuard guard(c->device);
   SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->err_dev) {
+    int err = 0;
+    SGP_CUDA(c, cudaMemcpy(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      SGP_CUDA(c, cudaMemset(c->err_dev, 0, sizeof(int)));
+      c->have_state = false;
+      return fail(c, SGP_ETIMEOUT, "a tile-load wait of line-pass variant 4 gave up; the state is undefined "
+                                   "until it is set again");
+    }
+  }
   return SGP_OK;
 }
 
@@ -1970,6 +2051,7 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   for (void* t : c->tw) dev_free(c, t);
   for (void* t : c->tw4) dev_free(c, t);
   dev_free(c, c->t_dev);
+  dev_free(c, c->err_dev);
   dev_free(c, c->mp_dev);
   dev_free(c, c->partials);
   dev_free(c, c->obs_dev);

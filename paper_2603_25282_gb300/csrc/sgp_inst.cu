@@ -205,6 +205,59 @@ cudaError_t launch_linepass_v<Real, V>(int N, const LPassArgs<Real>& a, int plan
   }
 }
 
+#if SGP_LINE_TMA
+// line-pass variant 4 (FP32): geometry 1 with the tile loaded by tensor
+// copies; compiled with variant 1, whose geometry it shares
+static_assert(sizeof(Real) == 4, "tensor-copy tile loads are FP32 only");
+
+template <int N>
+static cudaError_t linepass_tma_prepare_n() {
+  constexpr int E = elems_per_thread<Real, N>();
+  static int done = -1;
+  return prepare(k_linepass_tma<Real, N, E, 1>, LCfg<Real, N, E, 1>::SMEM + LCfg<Real, N, E, 1>::TAB, &done);
+}
+
+template <int N>
+static cudaError_t linepass_tma_n(const LPassArgs<Real>& a, const CUtensorMap& map, int planes, int members,
+                                  cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef LCfg<Real, N, E, 1> Cfg;
+  cudaError_t e = linepass_tma_prepare_n<N>();
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
+  const size_t smem = Cfg::SMEM + line_table_bytes<Cfg>(a.mode, a.axis);
+  k_linepass_tma<Real, N, E, 1><<<grid, Cfg::THREADS, smem, s>>>(a, map);
+  return cudaGetLastError();
+}
+
+PassGeom linepass_geom_tma(int N) { return linepass_geom_v<Real, 1>(N); }
+
+cudaError_t prepare_linepass_tma(int N) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return linepass_tma_prepare_n<NN>();
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_linepass_tma(int N, const LPassArgs<Real>& a, const CUtensorMap& map, int planes,
+                                int members, cudaStream_t s) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return linepass_tma_n<NN>(a, map, planes, members, s);
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+#endif
+
 #if SGP_VAR == 0
 template <int N>
 static cudaError_t obs_line_n(const ObsLArgs<Real>& a, int planes, int members,

@@ -20,6 +20,8 @@
 // m = 2..-2, with d the real spin-2 rotation matrix below.  The same
 // factorisation gives exp(-i c1 d F.f) of Eq. (solution2).
 #pragma once
+#include <cuda.h>   // CUtensorMap (the TMA tile loads of line-pass variant 4)
+
 #include "sgp_fft.cuh"
 
 namespace sgp {
@@ -71,6 +73,11 @@ struct LPassArgs {
   long long mt_member;
   const cplx<R>* kz;          // exp(-i nu_z^2 d/2) - 1 (3D only)
   R inv_hi, inv_lo;           // 1/(NX NY [NZ]) as an unevaluated sum hi + lo
+  // TMA tile loads (line-pass variant 4): the first member's index in the
+  // batch (tensor coordinate of component c of member m: (mc0 + m) * 5 + c)
+  // and the word a bounded wait that gave up sets
+  int mc0;
+  int* err;
 };
 
 // Entry layout of the per-mode table of the linear flow over delta, indexed
@@ -648,13 +655,95 @@ __device__ __forceinline__ void mix_entry(cplx<R> (&v)[5], const LPassArgs<R>& a
   }
 }
 
+// ----------------------------------------------------------------------------
+// TMA tile loads of the line pass (variant 4)
+// ----------------------------------------------------------------------------
+// The tile of a line pass is TILE columns x N line elements of each
+// component: at a 512^2 grid, 32 bytes of each of 512 rows 4 KB apart.  In
+// variant 4 one thread moves it into shared memory with tensor copies
+// (cp.async.bulk.tensor over a 4D map of the field, [comp*member][z][y][x],
+// 8-byte elements), two components in flight in the two exchange buffers,
+// and the threads read their elements from there; the completion is
+// tracked by an mbarrier (transaction bytes) per buffer.  A box holds at
+// most 256 elements along each dimension, so a line of N > 256 elements is
+// tma_rows<N>() rows per box, N / tma_rows<N>() boxes.
+template <int N>
+__host__ __device__ constexpr int tma_rows() {
+  int d = 1;
+  while (N % d != 0 || N / d > 256) ++d;
+  return N / d;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity, at most max_cycles of clock64;
+// false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, long long max_cycles) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity))
+    if (clock64() - t0 > max_cycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2,
+                                             int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
+          reinterpret_cast<unsigned long long>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// the bulk groups committed before the last `n` have finished reading shared memory
+template <int n>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(n) : "memory");
+}
+// every committed bulk group is complete (its writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// shared-memory writes of this thread visible to the tensor copies that follow
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// limit of a tile-load wait: about a second at the GPU's clock
+constexpr long long kTmaWaitCycles = 2000000000LL;
+
 // Body of the line pass for block (bx, plane, member): the CTA's columns
 // are bx * TILE .. bx * TILE + TILE - 1 of plane `plane` (the z slice for
 // y-lines, the y row for z-lines) of member `member`.  Called by k_linepass
 // with the block's own coordinates and by the persistent ensemble kernel.
-template <typename R, int N, int E, int G, bool CG = false>
+template <typename R, int N, int E, int G, bool CG = false, bool TMA = false>
 __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int plane, int member,
-                                              unsigned char* smem_raw) {
+                                              unsigned char* smem_raw,
+                                              const CUtensorMap* tmap = nullptr) {
   typedef cplx<R> C;
   typedef LCfg<R, N, E, G> Cfg;
   constexpr int T = Cfg::T;
@@ -721,11 +810,53 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
             (valid ? xcol : 0) + (size_t)i * a.line_stride;
   const size_t step = (size_t)T * a.line_stride;
   C v[5][E];
+  if constexpr (TMA) {
+    // the five components through the two exchange buffers (staged as
+    // [line element][TILE], 2 x TILE x N <= 2 x TILE x LP elements); columns
+    // past the grid's edge come in as zeros
+    static_assert(sizeof(R) == 4 && TILE % 2 == 0, "tile loads: FP32, an even number of columns");
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    constexpr int RB = tma_rows<N>();
+    constexpr unsigned BYTES = (unsigned)(TILE * N * sizeof(C));
+    const int x0 = bx * TILE;
+    const int mc = (a.mc0 + member) * 5;
+    auto issue = [&](int c) {
+      C* st = xb + (c & 1) * TILE * N;
+      mbar_expect_tx(&s_bar[c & 1], BYTES);
 #pragma unroll
-  for (int c = 0; c < 5; ++c)
+      for (int b = 0; b < N / RB; ++b) {
+        if (a.axis == 1) tma_load_4d(st + b * RB * TILE, tmap, &s_bar[c & 1], x0, b * RB, plane, mc + c);
+        else tma_load_4d(st + b * RB * TILE, tmap, &s_bar[c & 1], x0, plane, b * RB, mc + c);
+      }
+    };
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      issue(0);
+      issue(1);
+    }
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      v[c][e] = valid ? ld_field<CG>(base + (size_t)c * a.ntot + e * step) : mkc((R)0, (R)0);
+    for (int c = 0; c < 5; ++c) {
+      if (!mbar_wait(&s_bar[c & 1], (unsigned)((c >> 1) & 1), kTmaWaitCycles) && a.err) atomicExch(a.err, 1);
+      const C* st = xb + (c & 1) * TILE * N;
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = st[(i + T * e) * TILE + col];
+      if (c + 2 < 5) {
+        __syncthreads();                // every thread has read the buffer
+        if (threadIdx.x == 0) issue(c + 2);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        v[c][e] = valid ? ld_field<CG>(base + (size_t)c * a.ntot + e * step) : mkc((R)0, (R)0);
+  }
   C* b0 = xb + col * Cfg::LP;
   const int bstride = TILE * Cfg::LP;
   if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
@@ -766,7 +897,37 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
     }
   }
   if (a.mode & LP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
-  if (valid) {
+  if constexpr (TMA) {
+    // the five components out through the two exchange buffers: each is
+    // written there, then stored by tensor copies (columns past the grid's
+    // edge are not written); a buffer is written again once the copy that
+    // read it is done
+    constexpr int RB = tma_rows<N>();
+    const int x0 = bx * TILE;
+    const int mc = (a.mc0 + member) * 5;
+    __syncthreads();                    // the exchanges' reads of the buffers are done
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      C* st = xb + (c & 1) * TILE * N;
+      if (c >= 2) {
+        if (threadIdx.x == 0) bulk_wait_read<1>();     // the copy of component c - 2 read the buffer
+        __syncthreads();
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) st[(i + T * e) * TILE + col] = v[c][e];
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < N / RB; ++b) {
+          if (a.axis == 1) tma_store_4d(tmap, st + b * RB * TILE, x0, b * RB, plane, mc + c);
+          else tma_store_4d(tmap, st + b * RB * TILE, x0, plane, b * RB, mc + c);
+        }
+        bulk_commit();
+      }
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+  } else if (valid) {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
 #pragma unroll
@@ -779,6 +940,14 @@ __global__ void __launch_bounds__(LCfg<R, N, E, G>::THREADS, LCfg<R, N, E, G>::M
 k_linepass(LPassArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   linepass_body<R, N, E, G>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// variant 4: the same pass with the tile loaded by tensor copies
+template <typename R, int N, int E, int G>
+__global__ void __launch_bounds__(LCfg<R, N, E, G>::THREADS, LCfg<R, N, E, G>::MINB)
+k_linepass_tma(LPassArgs<R> a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_tma[];    // tensor copies land 128-byte aligned
+  linepass_body<R, N, E, G, false, true>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma, &tmap);
 }
 
 // ----------------------------------------------------------------------------

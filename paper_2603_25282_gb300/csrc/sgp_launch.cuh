@@ -42,7 +42,9 @@ inline bool supported_n(int n) {
 //      three stages instead of 6*2*2*2*2 in five), in CTAs of 128 threads
 //      (x-pass geometry 1, line-pass geometry 2: a thread holds 120
 //      registers of field data)
-constexpr int kVariants = 4;
+//   4  FP32 only.  Line pass: geometry 1 with the tile loaded by tensor
+//      copies (TMA) into shared memory; x-pass: the same as variant 1
+constexpr int kVariants = 5;
 
 template <typename R, int N, int V>
 constexpr int variant_elems() {
@@ -51,13 +53,13 @@ constexpr int variant_elems() {
 // geometry of variant V for the x-pass (PART 0) and the line pass (PART 1)
 template <int N, int V, int PART>
 constexpr int variant_geom() {
-  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : V;
+  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : V == 4 ? 1 : V;
 }
 
 // Does variant V exist for line length N (prec_bytes 4 or 8)?
 inline bool variant_exists(int prec_bytes, int N, int V) {
   if (!supported_n(N) || V < 0 || V >= kVariants) return false;
-  if (V == 3) return prec_bytes == 4;
+  if (V == 3 || V == 4) return prec_bytes == 4;
   return true;
 }
 // Elements per thread of variant V (the twiddle table layout depends on it).
@@ -83,7 +85,26 @@ cudaError_t launch_xpass_v(int N, const XPassArgs<R>& a, int members, cudaStream
 template <typename R, int V>
 cudaError_t launch_linepass_v(int N, const LPassArgs<R>& a, int planes, int members,
                               cudaStream_t s);
+// Variant 4 of the line pass (tile loads by tensor copies over `map`).
+cudaError_t launch_linepass_tma(int N, const LPassArgs<float>& a, const CUtensorMap& map, int planes,
+                                int members, cudaStream_t s);
+cudaError_t prepare_linepass_tma(int N);
+PassGeom linepass_geom_tma(int N);
 
+// x-pass variant 4 is variant 1; the line pass has its own
+#define SGP_VARIANT_SWITCH_X(V, CALL, FAIL)                  \
+  switch (V) {                                               \
+    case 0: return CALL(0);                                  \
+    case 1: return CALL(1);                                  \
+    case 2: return CALL(2);                                  \
+    case 3:                                                  \
+      if constexpr (sizeof(R) == 4) return CALL(3);          \
+      return FAIL;                                           \
+    case 4:                                                  \
+      if constexpr (sizeof(R) == 4) return CALL(1);          \
+      return FAIL;                                           \
+    default: return FAIL;                                    \
+  }
 #define SGP_VARIANT_SWITCH(V, CALL, FAIL)                    \
   switch (V) {                                               \
     case 0: return CALL(0);                                  \
@@ -98,11 +119,13 @@ cudaError_t launch_linepass_v(int N, const LPassArgs<R>& a, int planes, int memb
 template <typename R>
 inline PassGeom xpass_geom(int N, int V = 0) {
 #define SGP_C(v) xpass_geom_v<R, v>(N)
-  SGP_VARIANT_SWITCH(V, SGP_C, (PassGeom{0, 0, 0}))
+  SGP_VARIANT_SWITCH_X(V, SGP_C, (PassGeom{0, 0, 0}))
 #undef SGP_C
 }
 template <typename R>
 inline PassGeom linepass_geom(int N, int V = 0) {
+  if constexpr (sizeof(R) == 4)
+    if (V == 4) return linepass_geom_tma(N);
 #define SGP_C(v) linepass_geom_v<R, v>(N)
   SGP_VARIANT_SWITCH(V, SGP_C, (PassGeom{0, 0, 0}))
 #undef SGP_C
@@ -112,11 +135,13 @@ inline PassGeom linepass_geom(int N, int V = 0) {
 template <typename R>
 inline cudaError_t prepare_xpass(int N, int V = 0) {
 #define SGP_C(v) prepare_xpass_v<R, v>(N)
-  SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
+  SGP_VARIANT_SWITCH_X(V, SGP_C, cudaErrorInvalidValue)
 #undef SGP_C
 }
 template <typename R>
 inline cudaError_t prepare_linepass(int N, int V = 0) {
+  if constexpr (sizeof(R) == 4)
+    if (V == 4) return prepare_linepass_tma(N);
 #define SGP_C(v) prepare_linepass_v<R, v>(N)
   SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
 #undef SGP_C
@@ -124,9 +149,10 @@ inline cudaError_t prepare_linepass(int N, int V = 0) {
 template <typename R>
 inline cudaError_t launch_xpass(int N, int V, const XPassArgs<R>& a, int members, cudaStream_t s) {
 #define SGP_C(v) launch_xpass_v<R, v>(N, a, members, s)
-  SGP_VARIANT_SWITCH(V, SGP_C, cudaErrorInvalidValue)
+  SGP_VARIANT_SWITCH_X(V, SGP_C, cudaErrorInvalidValue)
 #undef SGP_C
 }
+// Variants 0-3 of the line pass (variant 4 goes through launch_linepass_tma).
 template <typename R>
 inline cudaError_t launch_linepass(int N, int V, const LPassArgs<R>& a, int planes, int members,
                                    cudaStream_t s) {
@@ -135,6 +161,7 @@ inline cudaError_t launch_linepass(int N, int V, const LPassArgs<R>& a, int plan
 #undef SGP_C
 }
 #undef SGP_VARIANT_SWITCH
+#undef SGP_VARIANT_SWITCH_X
 
 // Observables kernels (default geometry only).
 template <typename R>

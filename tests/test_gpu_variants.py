@@ -97,7 +97,8 @@ def test_autotune_keeps_state_and_matches_oracle(prec):
         assert sgp.variant_exists(prec, n[a], plan[a])
         assert ms[a][plan[a]] is not None and ms[a][plan[a]] > 0
         for v in range(sgp.N_VARIANTS):
-            assert (ms[a][v] is not None) == sgp.variant_exists(prec, n[a], v)
+            timed = sgp.variant_exists(prec, n[a], v) and not (a == 0 and v == 4)
+            assert (ms[a][v] is not None) == timed
     assert ms[2] == [None] * sgp.N_VARIANTS
     assert c.autotune(reps=5) == plan                     # cached
     c.step(20, 1e-3, "ts4")
