@@ -123,19 +123,28 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def measured_instr(wl, kernel, plan, key="thread_instr_per_point"):
-    """Instructions per grid point of one launch of `kernel` from the
-    committed ncu counts (thread instructions: executed warp instructions x
-    32 / points; or the FP64 arithmetic instructions), or None when the
-    kernels or the plan differ from the counted ones."""
+def _traffic_entry(wl, kernel, plan, key):
+    """An entry of the committed ncu counts (profiles/traffic.json) for the
+    workload's kernel, or None when the pass-kernel sources or the workload's
+    kernel variants differ from the counted ones."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
     except Exception:
         return None
-    if tr.get("csrc_sha256_16") != csrc_hash() or list(tr.get("plan", [])) != list(plan):
+    if tr.get("csrc_sha256_16") != csrc_hash():
+        return None
+    if list(tr.get("plans", {}).get(wl, [])) != list(plan):
         return None
     return tr.get(key, {}).get("%s:%s" % (wl, kernel))
+
+
+def measured_instr(wl, kernel, plan, key="thread_instr_per_point"):
+    """Instructions per grid point of one launch of `kernel` from the
+    committed ncu counts (thread instructions: executed warp instructions x
+    32 / points; or the FP64 arithmetic instructions), or None when the
+    kernels or the plan differ from the counted ones."""
+    return _traffic_entry(wl, kernel, plan, key)
 
 
 def sm_max_mhz():
@@ -150,16 +159,7 @@ def measured_traffic(wl, kernel, plan):
     """DRAM bytes per launch from the committed ncu capture, or None when the
     kernels or the kernel variants differ from the captured ones (or none
     exists)."""
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f)
-    except Exception:
-        return None
-    if tr.get("csrc_sha256_16") != csrc_hash():
-        return None
-    if list(tr.get("plan", [])) != list(plan):
-        return None
-    return tr.get("bytes_per_launch", {}).get("%s:%s" % (wl, kernel))
+    return _traffic_entry(wl, kernel, plan, "bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------

@@ -31,17 +31,23 @@ def test_algorithmic_bytes_per_point_step(bench):
 def test_committed_traffic_matches_its_kernels_and_plan(bench):
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         tr = json.load(f)
-    plan = tr["plan"]
+    plans = tr["plans"]
     if tr["csrc_sha256_16"] != bench.csrc_hash():
         # the kernels changed since the capture: the bench reports no traffic
-        assert bench.measured_traffic("2d512_ts4_f32", "xpass", plan) is None
+        assert bench.measured_traffic("2d512_ts4_f32", "xpass", plans["2d512_ts4_f32"]) is None
         pytest.skip("pass kernels changed since the committed DRAM counters")
     for key, val in tr["bytes_per_launch"].items():
         wl, kern = key.split(":")
-        assert bench.measured_traffic(wl, kern, plan) == val
+        assert bench.measured_traffic(wl, kern, plans[wl]) == val
         # within 15% of the algorithmic one read + one write of the field
         n, L, prm, scheme, dt, prec, batch = bench.WORKLOADS[wl]
         alg = 2 * batch * 5 * n[0] * n[1] * (8 if prec == "f32" else 16)
         assert 0.8 * alg < val < 1.15 * alg
+    for key in list(tr["thread_instr_per_point"]) + list(tr["dp_instr_per_point"]):
+        wl, kern = key.split(":")
+        assert wl in plans
+    plan = plans["2d512_ts4_f32"]
     other = [v + 1 if k == 0 else v for k, v in enumerate(plan)]
     assert bench.measured_traffic("2d512_ts4_f32", "xpass", other) is None
+    assert bench.measured_instr("2d512_ts4_f64", "xpass", plans["2d512_ts4_f64"],
+                                "dp_instr_per_point") == tr["dp_instr_per_point"]["2d512_ts4_f64:xpass"]
