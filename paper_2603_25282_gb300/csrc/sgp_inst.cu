@@ -214,7 +214,7 @@ template <int N>
 static cudaError_t linepass_tma_prepare_n() {
   constexpr int E = elems_per_thread<Real, N>();
   static int done = -1;
-  return prepare(k_linepass_tma<Real, N, E, 1>, LCfg<Real, N, E, 1>::SMEM + LCfg<Real, N, E, 1>::TAB, &done);
+  return prepare(k_linepass_tma<Real, N, E, 1>, LCfg<Real, N, E, 1>::TSMEM + LCfg<Real, N, E, 1>::TAB, &done);
 }
 
 template <int N>
@@ -225,7 +225,7 @@ static cudaError_t linepass_tma_n(const LPassArgs<Real>& a, const CUtensorMap& m
   cudaError_t e = linepass_tma_prepare_n<N>();
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
-  const size_t smem = Cfg::SMEM + line_table_bytes<Cfg>(a.mode, a.axis);
+  const size_t smem = Cfg::TSMEM + line_table_bytes<Cfg>(a.mode, a.axis);
   k_linepass_tma<Real, N, E, 1><<<grid, Cfg::THREADS, smem, s>>>(a, map);
   return cudaGetLastError();
 }

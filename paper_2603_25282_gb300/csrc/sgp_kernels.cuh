@@ -586,6 +586,17 @@ struct LCfg {
   // 3D z-lines: TILE entries and the N z factors
   static constexpr size_t TABZ = (size_t)TILE * MT_STRIDE * sizeof(R) + (size_t)N * sizeof(cplx<R>);
   static_assert(SMEM + TAB <= 227 * 1024 && TABZ <= TAB, "line pass shared memory");
+  // variant 4 (tile loads by tensor copies): TSTG components in flight, as
+  // many (at most 4) as keep two CTAs on an SM; the staging buffers share
+  // the exchange buffers' region, enlarged to TREG elements if needed
+  static constexpr int XB = NB * TILE * LP;
+  static constexpr size_t treg(int k) { return (size_t)(k * TILE * N > XB ? k * TILE * N : XB); }
+  static constexpr bool tfits(int k) {
+    return 2 * (sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * treg(k) + TAB + 1024) <= 226 * 1024;
+  }
+  static constexpr int TSTG = tfits(4) ? 4 : tfits(3) ? 3 : 2;
+  static constexpr size_t TREG = treg(TSTG);
+  static constexpr size_t TSMEM = sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * TREG;
 };
 
 // dynamic shared memory added to a line pass for its table copies
@@ -765,7 +776,7 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
   //     then the z factors kz[0..N).
   constexpr int HN = N / 2 + 1;
   constexpr int GR = MT_STRIDE * (int)sizeof(R) / 16;          // 16-byte pieces per entry
-  R* smt = reinterpret_cast<R*>(xb + Cfg::NB * TILE * Cfg::LP);
+  R* smt = reinterpret_cast<R*>(xb + (TMA ? Cfg::TREG : (size_t)Cfg::XB));
   const bool stab = (a.mode & LP_MIX) && a.axis == 1;
   const bool stabz = (a.mode & LP_MIX) && a.axis == 2;
   if (stabz) {
@@ -811,43 +822,42 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
   const size_t step = (size_t)T * a.line_stride;
   C v[5][E];
   if constexpr (TMA) {
-    // the five components through the two exchange buffers (staged as
-    // [line element][TILE], 2 x TILE x N <= 2 x TILE x LP elements); columns
-    // past the grid's edge come in as zeros
+    // the five components through Cfg::TSTG staging buffers in the exchange
+    // buffers' region (each [line element][TILE]); columns past the grid's
+    // edge come in as zeros
     static_assert(sizeof(R) == 4 && TILE % 2 == 0, "tile loads: FP32, an even number of columns");
-    __shared__ __align__(8) unsigned long long s_bar[2];
+    constexpr int NSTG = Cfg::TSTG;
+    __shared__ __align__(8) unsigned long long s_bar[NSTG];
     constexpr int RB = tma_rows<N>();
     constexpr unsigned BYTES = (unsigned)(TILE * N * sizeof(C));
     const int x0 = bx * TILE;
     const int mc = (a.mc0 + member) * 5;
     auto issue = [&](int c) {
-      C* st = xb + (c & 1) * TILE * N;
-      mbar_expect_tx(&s_bar[c & 1], BYTES);
+      C* st = xb + (c % NSTG) * TILE * N;
+      mbar_expect_tx(&s_bar[c % NSTG], BYTES);
 #pragma unroll
       for (int b = 0; b < N / RB; ++b) {
-        if (a.axis == 1) tma_load_4d(st + b * RB * TILE, tmap, &s_bar[c & 1], x0, b * RB, plane, mc + c);
-        else tma_load_4d(st + b * RB * TILE, tmap, &s_bar[c & 1], x0, plane, b * RB, mc + c);
+        if (a.axis == 1) tma_load_4d(st + b * RB * TILE, tmap, &s_bar[c % NSTG], x0, b * RB, plane, mc + c);
+        else tma_load_4d(st + b * RB * TILE, tmap, &s_bar[c % NSTG], x0, plane, b * RB, mc + c);
       }
     };
     if (threadIdx.x == 0) {
-      mbar_init(&s_bar[0], 1);
-      mbar_init(&s_bar[1], 1);
+      for (int k = 0; k < NSTG; ++k) mbar_init(&s_bar[k], 1);
       mbar_fence_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      issue(0);
-      issue(1);
+      for (int k = 0; k < NSTG; ++k) issue(k);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      if (!mbar_wait(&s_bar[c & 1], (unsigned)((c >> 1) & 1), kTmaWaitCycles) && a.err) atomicExch(a.err, 1);
-      const C* st = xb + (c & 1) * TILE * N;
+      if (!mbar_wait(&s_bar[c % NSTG], (unsigned)((c / NSTG) & 1), kTmaWaitCycles) && a.err) atomicExch(a.err, 1);
+      const C* st = xb + (c % NSTG) * TILE * N;
 #pragma unroll
       for (int e = 0; e < E; ++e) v[c][e] = st[(i + T * e) * TILE + col];
-      if (c + 2 < 5) {
+      if (c + NSTG < 5) {
         __syncthreads();                // every thread has read the buffer
-        if (threadIdx.x == 0) issue(c + 2);
+        if (threadIdx.x == 0) issue(c + NSTG);
       }
     }
   } else {
