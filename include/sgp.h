@@ -54,7 +54,7 @@ typedef enum {
   SGP_EINVAL = 1,        /* bad argument (size, pointer, parameter, dt)   */
   SGP_ENOMEM = 2,        /* device or host allocation failed              */
   SGP_ECUDA = 3,         /* a CUDA runtime call failed (see last_error)   */
-  SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up (ensembles) */
+  SGP_ETIMEOUT = 4,      /* a bounded device-side wait gave up (ensembles, tile loads) */
   SGP_ENONFINITE = 5,    /* a NaN/Inf was detected in the observables     */
   SGP_ESTATE = 6,        /* call out of order (e.g. step before set_state)*/
   SGP_EUNSUPPORTED = 7,  /* valid request the library does not implement */
@@ -492,7 +492,10 @@ sgp_status sgp_observables_static(int dim, const int* n, const double* L, int ba
                                   sgp_obs* out);
 
 /* Wait for all work issued on the context stream.  Errors: SGP_EINVAL for
- * NULL; SGP_ECUDA with the first asynchronous failure. */
+ * NULL; SGP_ECUDA with the first asynchronous failure; SGP_ETIMEOUT when a
+ * bounded wait of line-pass variant 4 for its tile's tensor copies gave up
+ * since the last call (the state is then undefined until it is set again;
+ * the word is cleared). */
 sgp_status sgp_synchronize(sgp_ctx* ctx);
 
 /* Number of kernels this context has launched so far (for accounting; graph
