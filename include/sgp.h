@@ -323,7 +323,9 @@ sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
  * next sgp_set_state, sgp_set_params(_batch), sgp_step, sgp_substep or
  * sgp_record.  Memory: ceil(nsteps/interval) states for the checkpoints and
  * interval*(substeps per step) + 1 states (3 for TS2, 7 for TS4) for one
- * recomputed segment in sgp_backward.  Errors: SGP_EINVAL for nsteps <= 0,
+ * recomputed segment in sgp_backward, and a second such buffer when it can
+ * be had (the next segment is then recomputed on a second stream during the
+ * sweep through the current one).  Errors: SGP_EINVAL for nsteps <= 0,
  * interval < 0 or dt/scheme as in sgp_step; SGP_ESTATE before
  * sgp_set_state; SGP_ENOMEM/SGP_ECUDA on allocation or launch failure. */
 sgp_status sgp_record(sgp_ctx* ctx, long long nsteps, double dt, int scheme,
@@ -339,7 +341,9 @@ sgp_status sgp_record(sgp_ctx* ctx, long long nsteps, double dt, int scheme,
  * partial derivatives dJ/d(Omega, gamma, c0, c1, c2) through the dynamics
  * into dparams[5*m + 0..4] for member m (host memory; a dependence of J on
  * Omega through the frame R(T) is the caller's).  Each segment is recomputed
- * from its checkpoint.  Synchronises the context stream.  The record stays
+ * from its checkpoint (overlapping the sweep through the segment after it
+ * when the second segment buffer fits; same result).  Synchronises the
+ * context stream.  The record stays
  * valid (several objectives can be differentiated).  Errors: SGP_EINVAL for
  * NULL buffers; SGP_ESTATE without a valid record; SGP_ECUDA. */
 sgp_status sgp_backward(sgp_ctx* ctx, const void* g_T, int g_T_on_device, void* g_0,

@@ -279,7 +279,26 @@ struct AdjRec {
   double graph_dt = 0.0;
   int graph_scheme = -1;
   const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // pipelined sweep: a second segment buffer, and captured recomputations
+  // [0][b] and adjoint sweeps [1][b] of a full segment in buffer b
+  void* seg2 = nullptr;
+  size_t seg2_cap = 0;
+  cudaGraphExec_t pgraph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  long long pgraph_launches[2][2] = {{0, 0}, {0, 0}};
+  const void* pgraph_key[2][2][6] = {};
+  long long pgraph_len = 0;
+  double pgraph_dt = 0.0;
+  int pgraph_scheme = -1;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // start, recomputed[2], swept[2]
 };
+
+void free_adj_pgraphs(AdjRec& r) {
+  for (auto& row : r.pgraph)
+    for (auto& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
 
 // Device allocator of a context: the caller's (sgp_set_allocator) or
 // cudaMalloc/cudaFree when none was set.
@@ -466,6 +485,7 @@ void free_graphs(sgp_ctx* c) {
 }
 
 void free_tables(sgp_ctx* c) {
+  free_adj_pgraphs(c->adj);
   if (c->adj.graph) {            // the captured adjoint segment points at the tables
     cudaGraphExecDestroy(c->adj.graph);
     c->adj.graph = nullptr;
@@ -558,10 +578,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tensor map of the FP32 field for the line pass along `axis` (variant 4):
 // 4D, [5 * batch][nz][ny][nx] of 8-byte elements, x innermost; the box is
 // TILE columns by tma_rows(N) line elements (y for axis 1, z for axis 2).
-// The map holds the field's address: it is made again when the field
-// buffer changes (the autotuner steps a scratch copy).
-sgp_status ensure_tmap(sgp_ctx* c, int axis) {
-  if (c->tmap_field[axis] == c->field) return SGP_OK;
+// The map holds the address of the batch it covers (base): the context's
+// field, the autotuner's scratch copy, or a buffer of the adjoint sweep; it
+// is made again whenever a pass works on another one (a map travels by
+// value into the kernel's parameters, also into captured graphs).
+sgp_status ensure_tmap(sgp_ctx* c, int axis, void* base) {
+  if (c->tmap_field[axis] == base) return SGP_OK;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(c, SGP_EUNSUPPORTED, "the driver has no tensor-map encoder (variant 4)");
   const int N = c->n[axis];
@@ -577,11 +599,11 @@ sgp_status ensure_tmap(sgp_ctx* c, int axis) {
   const cuuint64_t strides[3] = {nx * 8, nx * ny * 8, nx * ny * nz * 8};
   const cuuint32_t box[4] = {tile, axis == 1 ? (cuuint32_t)rows : 1u, axis == 2 ? (cuuint32_t)rows : 1u, 1u};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = enc(&c->tmap[axis], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c->field, dims, strides, box, estr,
+  const CUresult r = enc(&c->tmap[axis], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(c, SGP_ECUDA, "tensor map for axis %d: driver error %d", axis, (int)r);
-  c->tmap_field[axis] = c->field;
+  c->tmap_field[axis] = base;
   return SGP_OK;
 }
 
@@ -678,7 +700,9 @@ sgp_status line_pass_on(sgp_ctx* c, void* field, int axis, int mode, const LinTa
   }
   if constexpr (sizeof(R) == 4) {
     if (c->var[axis] == 4) {
-      SGP_TRY(ensure_tmap(c, axis));
+      // the batch the window's field belongs to (member coordinates mc0 + m)
+      char* batch_base = (char*)field - (size_t)c->win0 * 5 * c->ntot * c->elem;
+      SGP_TRY(ensure_tmap(c, axis, batch_base));
       c->launches++;
       ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
       SGP_CUDA(c, launch_linepass_tma(c->n[axis], a, c->tmap[axis], planes, window_members(c), c->stream));
@@ -1013,8 +1037,12 @@ sgp_status ensure_buf(sgp_ctx* c, void** p, size_t* cap, size_t bytes) {
 void free_adj(sgp_ctx* c) {
   AdjRec& r = c->adj;
   if (r.graph) cudaGraphExecDestroy(r.graph);
+  free_adj_pgraphs(r);
+  for (cudaEvent_t e : r.ev)
+    if (e) cudaEventDestroy(e);
   dev_free(c, r.ckpt);
   dev_free(c, r.seg);
+  dev_free(c, r.seg2);
   dev_free(c, r.g);
   dev_free(c, r.spec);
   dev_free(c, r.dp);
@@ -1130,14 +1158,11 @@ std::vector<SubRec> segment_substeps(int scheme, long long n, double dt) {
   return merged_substeps(scheme, n, dt);
 }
 
-// One segment: recompute the states from seg[0] substep by substep, then
-// carry g back through the substeps in reverse order.  Reads the segment
-// start time from the device clock.
+// The states of a segment recomputed from seg[0] substep by substep (the
+// segment start time from the device clock).
 template <typename R>
-sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs) {
-  AdjRec& r = c->adj;
+sgp_status emit_recompute(sgp_ctx* c, const std::vector<SubRec>& subs, char* seg) {
   const size_t sb = state_bytes(c);
-  char* seg = (char*)r.seg;
   for (size_t j = 0; j < subs.size(); ++j) {
     void* out = seg + sb * (j + 1);
     SGP_CUDA(c, cudaMemcpyAsync(out, seg + sb * j, sb, cudaMemcpyDeviceToDevice, c->stream));
@@ -1149,6 +1174,13 @@ sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs) {
       SGP_TRY(x_pass_on<R>(c, out, XP_INV, 0.0, 0.0));
     }
   }
+  return SGP_OK;
+}
+
+// g carried back through a recomputed segment's substeps in reverse order.
+template <typename R>
+sgp_status emit_adjoint(sgp_ctx* c, const std::vector<SubRec>& subs, const char* seg) {
+  const size_t sb = state_bytes(c);
   for (size_t j = subs.size(); j-- > 0;) {
     const void* phi_out = seg + sb * (j + 1);
     if (subs[j].kind == 'N')
@@ -1157,6 +1189,13 @@ sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs) {
       SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta));
   }
   return SGP_OK;
+}
+
+// One segment: the recomputation, then the adjoint sweep through it.
+template <typename R>
+sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs) {
+  SGP_TRY(emit_recompute<R>(c, subs, (char*)c->adj.seg));
+  return emit_adjoint<R>(c, subs, (const char*)c->adj.seg);
 }
 
 void free_adj_graph(sgp_ctx* c) {
@@ -1201,9 +1240,130 @@ sgp_status segment_graph(sgp_ctx* c, const std::vector<SubRec>& subs, cudaGraphE
   return SGP_OK;
 }
 
+// Captured recomputation (kind 0) or adjoint sweep (kind 1) of a full
+// segment in buffer b, issued on the current c->stream with the current
+// c->t_dev (cached per kind and buffer; rebuilt when the run, the buffers
+// or the tables change).
+template <typename R>
+sgp_status pipe_graph(sgp_ctx* c, int kind, int b, const std::vector<SubRec>& subs, char* seg,
+                      cudaGraphExec_t* out) {
+  AdjRec& r = c->adj;
+  const void* key[6] = {seg, r.g, r.spec, r.part, c->t_dev, c->stream};
+  if (r.pgraph_len != r.interval || r.pgraph_dt != r.dt || r.pgraph_scheme != r.scheme) {
+    free_adj_pgraphs(r);
+    r.pgraph_len = r.interval;
+    r.pgraph_dt = r.dt;
+    r.pgraph_scheme = r.scheme;
+  }
+  cudaGraphExec_t& g = r.pgraph[kind][b];
+  if (g && std::memcmp(key, r.pgraph_key[kind][b], sizeof key) == 0) {
+    *out = g;
+    return SGP_OK;
+  }
+  if (g) cudaGraphExecDestroy(g);
+  g = nullptr;
+  const long long launches0 = c->launches;
+  SGP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  sgp_status st = kind == 0 ? emit_recompute<R>(c, subs, seg) : emit_adjoint<R>(c, subs, seg);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  r.pgraph_launches[kind][b] = c->launches - launches0;
+  c->launches = launches0;
+  if (st != SGP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, SGP_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g = nullptr;
+    return fail(c, SGP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  std::memcpy(r.pgraph_key[kind][b], key, sizeof key);
+  *out = g;
+  return SGP_OK;
+}
+
+// Backward sweep with the recomputation of segment k - 1 running on a
+// second stream (cs_alt, with its own device time) while g is carried back
+// through segment k on the context stream.  The two use alternate segment
+// buffers: segment k's recomputation waits until the sweep through segment
+// k + 2 (the buffer's previous user) is done, and segment k's sweep waits
+// for its recomputation.  The kernels of a small grid fill a fraction of
+// the GPU, so the two streams overlap.  The operations and their order on
+// each buffer are those of the serial sweep, so is the result.
+template <typename R>
+sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full) {
+  AdjRec& r = c->adj;
+  const size_t sb = state_bytes(c);
+  if (!c->cs_alt) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_alt, cudaStreamNonBlocking));
+  if (!c->t_dev_alt) SGP_CUDA(c, dev_alloc(c, (void**)&c->t_dev_alt, sizeof(double)));
+  for (cudaEvent_t& e : r.ev)
+    if (!e) SGP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  char* segs[2] = {(char*)r.seg, (char*)r.seg2};
+  const bool graphs = c->use_graphs && !c->profiling;
+  // the recomputations start after the work already on the context stream
+  SGP_CUDA(c, cudaEventRecord(r.ev[0], c->stream));
+  SGP_CUDA(c, cudaStreamWaitEvent(c->cs_alt, r.ev[0], 0));
+  for (long long k = r.nck - 1; k >= 0; --k) {
+    const int b = (int)(k & 1);
+    const long long n = std::min(r.interval, r.nsteps - k * r.interval);
+    const double tk = r.t0 + (double)(k * r.interval) * r.dt;
+    const std::vector<SubRec> part = n == r.interval ? std::vector<SubRec>() : segment_substeps(r.scheme, n, r.dt);
+    const std::vector<SubRec>& subs = n == r.interval ? full : part;
+    // recomputation of segment k on the second stream
+    if (k + 2 < r.nck) SGP_CUDA(c, cudaStreamWaitEvent(c->cs_alt, r.ev[3 + b], 0));
+    std::swap(c->stream, c->cs_alt);
+    std::swap(c->t_dev, c->t_dev_alt);
+    sgp_status st = SGP_OK;
+    c->launches++;
+    k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, tk);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(segs[b], (const char*)r.ckpt + sb * (size_t)k, sb, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) {
+      st = fail(c, SGP_ECUDA, "segment start: %s", cudaGetErrorString(e));
+    } else if (n == r.interval && graphs) {
+      cudaGraphExec_t exec = nullptr;
+      st = pipe_graph<R>(c, 0, b, subs, segs[b], &exec);
+      if (st == SGP_OK && (e = cudaGraphLaunch(exec, c->stream)) != cudaSuccess)
+        st = fail(c, SGP_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+      c->launches += r.pgraph_launches[0][b];
+    } else {
+      st = emit_recompute<R>(c, subs, segs[b]);
+    }
+    if (st == SGP_OK && (e = cudaEventRecord(r.ev[1 + b], c->stream)) != cudaSuccess)
+      st = fail(c, SGP_ECUDA, "event: %s", cudaGetErrorString(e));
+    std::swap(c->stream, c->cs_alt);
+    std::swap(c->t_dev, c->t_dev_alt);
+    if (st != SGP_OK) return st;
+    // adjoint sweep through segment k on the context stream
+    SGP_CUDA(c, cudaStreamWaitEvent(c->stream, r.ev[1 + b], 0));
+    c->launches++;
+    k_set_time<<<1, 1, 0, c->stream>>>(c->t_dev, tk);
+    SGP_CUDA(c, cudaGetLastError());
+    if (n == r.interval && graphs) {
+      cudaGraphExec_t exec = nullptr;
+      SGP_TRY(pipe_graph<R>(c, 1, b, subs, segs[b], &exec));
+      SGP_CUDA(c, cudaGraphLaunch(exec, c->stream));
+      c->launches += r.pgraph_launches[1][b];
+    } else {
+      SGP_TRY(emit_adjoint<R>(c, subs, segs[b]));
+    }
+    SGP_CUDA(c, cudaEventRecord(r.ev[3 + b], c->stream));
+  }
+  // the second stream's last work is done before anything that follows
+  SGP_CUDA(c, cudaEventRecord(r.ev[1], c->cs_alt));
+  SGP_CUDA(c, cudaStreamWaitEvent(c->stream, r.ev[1], 0));
+  return SGP_OK;
+}
+
 // Backward sweep over the recorded trajectory: each segment is recomputed
 // from its checkpoint, then g is carried back through its substeps in
-// reverse order.  Full-length segments replay one captured graph.
+// reverse order.  Pipelined over two streams when a second segment buffer
+// fits (backward_sweep_pipelined); otherwise serial, full-length segments
+// replaying one captured graph.
 template <typename R>
 sgp_status backward_sweep(sgp_ctx* c) {
   AdjRec& r = c->adj;
@@ -1223,6 +1383,27 @@ sgp_status backward_sweep(sgp_ctx* c) {
       SGP_TRY(get_tables<R>(c, -st.delta, &t));
     }
   const std::vector<SubRec> full = segment_substeps(r.scheme, r.interval, r.dt);
+  // a second segment buffer for the pipelined sweep, if the memory is there
+  bool pipe = r.nck > 1;
+  if (pipe && r.seg2_cap < sb * per_seg) {
+    SGP_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, r.seg2);
+    r.seg2 = nullptr;
+    r.seg2_cap = 0;
+    if (dev_alloc(c, &r.seg2, sb * per_seg) == cudaSuccess) {
+      r.seg2_cap = sb * per_seg;
+    } else {
+      cudaGetLastError();
+      r.seg2 = nullptr;
+      pipe = false;
+    }
+  }
+  if (pipe) {
+    SGP_TRY(backward_sweep_pipelined<R>(c, full));
+    c->launches++;
+    SGP_CUDA(c, launch_reduce_params(r.part, nblocks, c->batch, r.dp, c->stream));
+    return SGP_OK;
+  }
   const bool graphs = c->use_graphs && !c->profiling;
   for (long long k = r.nck - 1; k >= 0; --k) {
     const long long n = std::min(r.interval, r.nsteps - k * r.interval);
@@ -1386,6 +1567,7 @@ sgp_status checked_steps(sgp_ctx* c, long long nsteps, double dt, int scheme) {
 // ----------------------------------------------------------------------------
 void drop_graphs(sgp_ctx* c) {
   free_graphs(c);
+  free_adj_pgraphs(c->adj);
   if (c->adj.graph) {
     cudaGraphExecDestroy(c->adj.graph);
     c->adj.graph = nullptr;
