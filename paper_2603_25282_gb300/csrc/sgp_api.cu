@@ -1116,16 +1116,19 @@ sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t
 }
 
 // g <- L(-d) g, and the Omega and gamma terms from the transforms of g and
-// of Phi_out
+// of Phi_out (phi_spec: that transform made already, else made here)
 template <typename R>
-sgp_status adjoint_linear(sgp_ctx* c, const void* phi, double delta) {
+sgp_status adjoint_linear(sgp_ctx* c, const void* phi, double delta, const void* phi_spec = nullptr) {
   AdjRec& r = c->adj;
-  SGP_CUDA(c, cudaMemcpyAsync(r.spec, phi, state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-  SGP_TRY(to_spectral<R>(c, r.spec));
+  if (!phi_spec) {
+    SGP_CUDA(c, cudaMemcpyAsync(r.spec, phi, state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    SGP_TRY(to_spectral<R>(c, r.spec));
+    phi_spec = r.spec;
+  }
   SGP_TRY(to_spectral<R>(c, r.g));
   LinParArgs<R> a{};
   a.g = (const cplx<R>*)r.g;
-  a.s = (const cplx<R>*)r.spec;
+  a.s = (const cplx<R>*)phi_spec;
   a.ntot = c->ntot;
   a.NX = c->n[0];
   a.NY = c->n[1];
@@ -1159,10 +1162,14 @@ std::vector<SubRec> segment_substeps(int scheme, long long n, double dt) {
 }
 
 // The states of a segment recomputed from seg[0] substep by substep (the
-// segment start time from the device clock).
+// segment start time from the device clock).  With spec (the pipelined
+// sweep), the transform of every linear substep's output goes there too
+// (one state per linear substep, in order), for the parameter terms of the
+// adjoint sweep.
 template <typename R>
-sgp_status emit_recompute(sgp_ctx* c, const std::vector<SubRec>& subs, char* seg) {
+sgp_status emit_recompute(sgp_ctx* c, const std::vector<SubRec>& subs, char* seg, char* spec = nullptr) {
   const size_t sb = state_bytes(c);
+  size_t nl = 0;
   for (size_t j = 0; j < subs.size(); ++j) {
     void* out = seg + sb * (j + 1);
     SGP_CUDA(c, cudaMemcpyAsync(out, seg + sb * j, sb, cudaMemcpyDeviceToDevice, c->stream));
@@ -1172,21 +1179,32 @@ sgp_status emit_recompute(sgp_ctx* c, const std::vector<SubRec>& subs, char* seg
       SGP_TRY(x_pass_on<R>(c, out, XP_FWD, 0.0, 0.0));
       SGP_TRY(linear_middle_on<R>(c, out, subs[j].delta));
       SGP_TRY(x_pass_on<R>(c, out, XP_INV, 0.0, 0.0));
+      if (spec) {
+        char* sp = spec + sb * nl++;
+        SGP_CUDA(c, cudaMemcpyAsync(sp, out, sb, cudaMemcpyDeviceToDevice, c->stream));
+        SGP_TRY(to_spectral<R>(c, sp));
+      }
     }
   }
   return SGP_OK;
 }
 
-// g carried back through a recomputed segment's substeps in reverse order.
+// g carried back through a recomputed segment's substeps in reverse order
+// (spec: the transforms the recomputation made, or null).
 template <typename R>
-sgp_status emit_adjoint(sgp_ctx* c, const std::vector<SubRec>& subs, const char* seg) {
+sgp_status emit_adjoint(sgp_ctx* c, const std::vector<SubRec>& subs, const char* seg,
+                        const char* spec = nullptr) {
   const size_t sb = state_bytes(c);
+  size_t nl = 0;
+  for (const SubRec& q : subs) nl += q.kind == 'L';
   for (size_t j = subs.size(); j-- > 0;) {
     const void* phi_out = seg + sb * (j + 1);
-    if (subs[j].kind == 'N')
+    if (subs[j].kind == 'N') {
       SGP_TRY(adjoint_nonlinear<R>(c, phi_out, subs[j].delta, subs[j].toff));
-    else
-      SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta));
+    } else {
+      --nl;
+      SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta, spec ? spec + sb * nl : nullptr));
+    }
   }
   return SGP_OK;
 }
@@ -1245,7 +1263,7 @@ sgp_status segment_graph(sgp_ctx* c, const std::vector<SubRec>& subs, cudaGraphE
 // c->t_dev (cached per kind and buffer; rebuilt when the run, the buffers
 // or the tables change).
 template <typename R>
-sgp_status pipe_graph(sgp_ctx* c, int kind, int b, const std::vector<SubRec>& subs, char* seg,
+sgp_status pipe_graph(sgp_ctx* c, int kind, int b, const std::vector<SubRec>& subs, char* seg, char* spec,
                       cudaGraphExec_t* out) {
   AdjRec& r = c->adj;
   const void* key[6] = {seg, r.g, r.spec, r.part, c->t_dev, c->stream};
@@ -1264,7 +1282,7 @@ sgp_status pipe_graph(sgp_ctx* c, int kind, int b, const std::vector<SubRec>& su
   g = nullptr;
   const long long launches0 = c->launches;
   SGP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  sgp_status st = kind == 0 ? emit_recompute<R>(c, subs, seg) : emit_adjoint<R>(c, subs, seg);
+  sgp_status st = kind == 0 ? emit_recompute<R>(c, subs, seg, spec) : emit_adjoint<R>(c, subs, seg, spec);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   r.pgraph_launches[kind][b] = c->launches - launches0;
@@ -1294,7 +1312,7 @@ sgp_status pipe_graph(sgp_ctx* c, int kind, int b, const std::vector<SubRec>& su
 // the GPU, so the two streams overlap.  The operations and their order on
 // each buffer are those of the serial sweep, so is the result.
 template <typename R>
-sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full) {
+sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full, size_t spec_off) {
   AdjRec& r = c->adj;
   const size_t sb = state_bytes(c);
   if (!c->cs_alt) SGP_CUDA(c, cudaStreamCreateWithFlags(&c->cs_alt, cudaStreamNonBlocking));
@@ -1302,6 +1320,7 @@ sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full)
   for (cudaEvent_t& e : r.ev)
     if (!e) SGP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   char* segs[2] = {(char*)r.seg, (char*)r.seg2};
+  char* specs[2] = {segs[0] + spec_off, segs[1] + spec_off};   // the linear substeps' transforms
   const bool graphs = c->use_graphs && !c->profiling;
   // the recomputations start after the work already on the context stream
   SGP_CUDA(c, cudaEventRecord(r.ev[0], c->stream));
@@ -1326,12 +1345,12 @@ sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full)
       st = fail(c, SGP_ECUDA, "segment start: %s", cudaGetErrorString(e));
     } else if (n == r.interval && graphs) {
       cudaGraphExec_t exec = nullptr;
-      st = pipe_graph<R>(c, 0, b, subs, segs[b], &exec);
+      st = pipe_graph<R>(c, 0, b, subs, segs[b], specs[b], &exec);
       if (st == SGP_OK && (e = cudaGraphLaunch(exec, c->stream)) != cudaSuccess)
         st = fail(c, SGP_ECUDA, "graph launch: %s", cudaGetErrorString(e));
       c->launches += r.pgraph_launches[0][b];
     } else {
-      st = emit_recompute<R>(c, subs, segs[b]);
+      st = emit_recompute<R>(c, subs, segs[b], specs[b]);
     }
     if (st == SGP_OK && (e = cudaEventRecord(r.ev[1 + b], c->stream)) != cudaSuccess)
       st = fail(c, SGP_ECUDA, "event: %s", cudaGetErrorString(e));
@@ -1345,11 +1364,11 @@ sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full)
     SGP_CUDA(c, cudaGetLastError());
     if (n == r.interval && graphs) {
       cudaGraphExec_t exec = nullptr;
-      SGP_TRY(pipe_graph<R>(c, 1, b, subs, segs[b], &exec));
+      SGP_TRY(pipe_graph<R>(c, 1, b, subs, segs[b], specs[b], &exec));
       SGP_CUDA(c, cudaGraphLaunch(exec, c->stream));
       c->launches += r.pgraph_launches[1][b];
     } else {
-      SGP_TRY(emit_adjoint<R>(c, subs, segs[b]));
+      SGP_TRY(emit_adjoint<R>(c, subs, segs[b], specs[b]));
     }
     SGP_CUDA(c, cudaEventRecord(r.ev[3 + b], c->stream));
   }
@@ -1383,23 +1402,31 @@ sgp_status backward_sweep(sgp_ctx* c) {
       SGP_TRY(get_tables<R>(c, -st.delta, &t));
     }
   const std::vector<SubRec> full = segment_substeps(r.scheme, r.interval, r.dt);
-  // a second segment buffer for the pipelined sweep, if the memory is there
+  // the pipelined sweep: two segment buffers, each with room for the
+  // transforms of the segment's linear substeps, if the memory is there
+  size_t nlin = 0;
+  for (const auto& q : seq) nlin += q.first == 'L';
+  const size_t pipe_bytes = sb * (per_seg + (size_t)r.interval * nlin);
   bool pipe = r.nck > 1;
-  if (pipe && r.seg2_cap < sb * per_seg) {
+  for (int k = 0; k < 2 && pipe; ++k) {
+    void** p = k ? &r.seg2 : &r.seg;
+    size_t* cap = k ? &r.seg2_cap : &r.seg_cap;
+    if (*cap >= pipe_bytes) continue;
     SGP_CUDA(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, r.seg2);
-    r.seg2 = nullptr;
-    r.seg2_cap = 0;
-    if (dev_alloc(c, &r.seg2, sb * per_seg) == cudaSuccess) {
-      r.seg2_cap = sb * per_seg;
+    dev_free(c, *p);
+    *p = nullptr;
+    *cap = 0;
+    if (dev_alloc(c, p, pipe_bytes) == cudaSuccess) {
+      *cap = pipe_bytes;
     } else {
       cudaGetLastError();
-      r.seg2 = nullptr;
+      *p = nullptr;
       pipe = false;
     }
   }
+  if (!pipe) SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, sb * per_seg));
   if (pipe) {
-    SGP_TRY(backward_sweep_pipelined<R>(c, full));
+    SGP_TRY(backward_sweep_pipelined<R>(c, full, sb * per_seg));
     c->launches++;
     SGP_CUDA(c, launch_reduce_params(r.part, nblocks, c->batch, r.dp, c->stream));
     return SGP_OK;
