@@ -1607,6 +1607,8 @@ sgp_status use_variant(sgp_ctx* c, int a, int v) {
   const int pb = c->prec == SGP_F32 ? 4 : 8;
   if (!variant_exists(pb, c->n[a], v))
     return fail(c, SGP_EINVAL, "variant %d does not exist for N = %d on axis %d", v, c->n[a], a);
+  if (v == 4 && !tensor_map_encoder())      // fetched now, not inside a later stream capture
+    return fail(c, SGP_EUNSUPPORTED, "the driver has no tensor-map encoder (variant 4)");
   if (v == 3 && !c->tw4[a]) {
     SGP_CUDA(c, cudaStreamSynchronize(c->stream));
     SGP_CUDA(c, dev_alloc(c, &c->tw4[a], (size_t)c->n[a] * sizeof(TwE<float>)));
@@ -1672,6 +1674,7 @@ sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
     for (int v = 0; v < kVariants && st == SGP_OK; ++v) {
       if (!variant_exists(pb, c->n[a], v)) continue;
       if (a == 0 && v == 4) continue;     // the x-pass of variant 4 is variant 1
+      if (v == 4 && !tensor_map_encoder()) continue;
       st = use_variant(c, a, v);
       if (st != SGP_OK) break;
       c->launches++;
