@@ -94,14 +94,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def bytes_per_point_step(dim, scheme, prec):
+def bytes_per_point_step(dim, scheme, prec, plan=(0, 0, 0)):
     """Algorithmic HBM bytes per grid-point-step: each pass reads and writes
     the five-component field once (s = 40 B FP32, 80 B FP64); the merged
-    steady state has 2 passes per (L, N) pair in 2D and 4 in 3D; TS2 has one
-    pair per step, TS4 three."""
+    steady state has 2 passes per (L, N) pair in 2D and 4 in 3D (2 with the
+    xy-plane pass, x-pass variant 5); TS2 has one pair per step, TS4 three."""
     s = 40 if prec == "f32" else 80
     pairs = 1 if scheme == "ts2" else 3
-    passes = 2 if dim == 2 else 4
+    passes = 2 if (dim == 2 or plan[0] == 5) else 4
     return 2 * s * passes * pairs, 2 * s
 
 
@@ -447,6 +447,8 @@ def run_ours(args, rank, world, local_rank):
     kinds = {k: v for k, v in prof.items() if k in ("xpass", "linepass_y", "linepass_z") and v[0]}
     dom = max(kinds, key=lambda k: kinds[k][1])
     dom_avg_ms = kinds[dom][1] / kinds[dom][0]
+    if dom == "xpass" and dim == 3 and plan[0] == 5:
+        dom = "xyplane"                       # x-pass variant 5: the xy-plane pass
     achieved = per_pass_bytes / (dom_avg_ms * 1e-3) / 1e9
     traffic = measured_traffic(wl, dom, plan)
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
@@ -479,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
                 "dp_instr_per_launch": dp_launch, "avg_launch_ms": dom_avg_ms,
                 "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved / hbm_peak, "bytes_per_launch": per_pass_bytes}}
-    bpp, bmin = bytes_per_point_step(dim, scheme, prec)
+    bpp, bmin = bytes_per_point_step(dim, scheme, prec, plan)
     step_gbs = bpp * pts * batch * args.steps / (ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers --------------------

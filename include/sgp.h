@@ -262,7 +262,8 @@ sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
 
 /* ---------------------------------------------------------------------
  * Kernel variants (FFT tile and radix schedules) and the autotuner.
- * Every pass kernel exists in up to five variants per line length N:
+ * Every pass kernel exists in up to five variants per line length N, and
+ * 3D grids have a sixth, plane-level variant of the x-pass:
  *   0  default: x-pass CTAs of about 256 threads (rows side by side), line
  *      pass up to 512 threads with TILE >= 4 (FP32) / 2 (FP64) columns;
  *   1  CTAs of about half the threads (line pass TILE down to 1);
@@ -272,14 +273,23 @@ sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
  *      6 then 4s) in CTAs of 128 threads;
  *   4  FP32 only: the line pass of variant 1 with its tile brought into
  *      shared memory by tensor copies (TMA) instead of per-thread loads
- *      (bit for bit variant 1); for the x-pass the same as variant 1.
+ *      (bit for bit variant 1); for the x-pass the same as variant 1;
+ *   5  FP32, x axis of 3D grids with NX = NY = 64 or 128 only: the
+ *      x-passes of sgp_step and sgp_substep become xy-plane passes, one
+ *      thread-block cluster of NX/16 CTAs per z plane that also does the
+ *      y transforms (the plane moves between the CTAs through distributed
+ *      shared memory), so a step runs no y-line passes: two passes per
+ *      linear/nonlinear pair instead of four.  Other x-passes (gradients,
+ *      observables) are those of variant 1.
  * A plan is one variant per axis (x-pass, y lines, z lines).  Variants
  * compute the same transforms with different rounding (variant 3 has a
  * different radix plan), so results agree to rounding, not bit for bit;
- * variant 4 agrees with variant 1 bit for bit.
+ * variant 4 agrees with variant 1 bit for bit, and variant 5 with variant
+ * 1 when the y axis runs variant 0, 1, 2 or 4.
  * ------------------------------------------------------------------- */
 /* 1 if variant v exists for line length n at precision prec, else 0
- * (also for arguments out of range).  Cannot fail. */
+ * (also for arguments out of range, and for variant 5, which depends on
+ * the whole grid: sgp_set_plan takes it as stated above).  Cannot fail. */
 int sgp_variant_exists(int prec, int n, int variant);
 /* Set the plan: variants[a] for axis a < dim.  Synchronises the context
  * stream; drops captured graphs.  SGP_EINVAL for a variant that does not
@@ -295,9 +305,10 @@ sgp_status sgp_get_plan(const sgp_ctx* ctx, int* variants);
  * variant must be at least 1.5% faster to replace a lower one).  The state
  * and the time are not changed.  Results are cached per process by
  * (device, precision, grid, batch); a cached plan is reused unless flags
- * has SGP_TUNE_FORCE or ms_out is given.  ms_out (may be NULL): 3 x 5
+ * has SGP_TUNE_FORCE or ms_out is given.  ms_out (may be NULL): 3 x 6
  * doubles, ms per step of [axis][variant], -1 where the variant or axis
- * does not exist and for variant 4 of the x-pass (which is variant 1).  Synchronises.  Allocates one field-sized scratch buffer
+ * does not exist and for variant 4 of the x-pass (which is variant 1).
+ * Synchronises.  Allocates one field-sized scratch buffer
  * for the duration of the call.  Errors: SGP_EINVAL for a NULL ctx or reps
  * outside [1, 1000]; SGP_ENOMEM / SGP_ECUDA for the scratch or a launch. */
 sgp_status sgp_autotune(sgp_ctx* ctx, int reps, int flags, double* ms_out);

@@ -32,7 +32,8 @@ UNITS = [
 ] + [
     ("inst_%s_%s_v%d" % (r[0:3], "xl"[part], v), "sgp_inst.cu",
      ["-DSGP_REAL=%s" % r, "-DSGP_PART=%d" % part, "-DSGP_VAR=%d" % v]
-     + (["-DSGP_LINE_TMA=1"] if (r, part, v) == ("float", 1, 1) else []))
+     + (["-DSGP_LINE_TMA=1"] if (r, part, v) == ("float", 1, 1) else [])
+     + (["-DSGP_XY_PLANE=1"] if (r, part, v) == ("float", 0, 1) else []))
     for r, nv in (("float", 4), ("double", 3)) for part in (0, 1) for v in range(nv)
 ]
 

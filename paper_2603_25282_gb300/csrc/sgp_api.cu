@@ -607,8 +607,18 @@ sgp_status ensure_tmap(sgp_ctx* c, int axis, void* base) {
   return SGP_OK;
 }
 
+// Is x-pass variant 5 usable here (3D FP32 grid with NX = NY = 64 or 128)?
+bool plane_ok(const sgp_ctx* c) {
+  return c->prec == SGP_F32 && c->dim == 3 && c->n[0] == c->n[1] && (c->n[0] == 64 || c->n[0] == 128);
+}
+// The steps' x-passes are xy-plane passes (x-pass variant 5): they also do
+// the y transforms, and the linear flow between them is the z-line pass
+// alone.  Not while passes are recorded for the persistent ensemble kernel,
+// which has no plane pass.
+bool plane_pass(const sgp_ctx* c) { return c->var[0] == 5 && !c->rec; }
+
 template <typename R>
-sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
+XPassArgs<R> x_args(const sgp_ctx* c, void* field, int mode, double delta, double t_off) {
   XPassArgs<R> a{};
   a.field = (cplx<R>*)field;
   a.tw = (const TwE<R>*)(c->var[0] == 3 ? c->tw4[0] : c->tw[0]);
@@ -626,6 +636,12 @@ sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_o
   a.mp = c->mp_dev + c->win0;
   a.t_base = c->t_dev;
   a.t_off = t_off;
+  return a;
+}
+
+template <typename R>
+sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
+  XPassArgs<R> a = x_args<R>(c, field, mode, delta, t_off);
   if (c->rec) {
     // recorded for the persistent ensemble kernel (default radix plan)
     PersistPass<R> p{};
@@ -645,8 +661,26 @@ sgp_status x_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_o
   return SGP_OK;
 }
 
+// xy-plane pass (x-pass variant 5, FP32): the x-pass with the y transforms,
+// one cluster per z plane of each member
+template <typename R>
+sgp_status xy_pass_on(sgp_ctx* c, void* field, int mode, double delta, double t_off) {
+  if constexpr (sizeof(R) != 4) {
+    return fail(c, SGP_EINVAL, "the xy-plane pass is FP32 only");
+  } else {
+    const XPassArgs<R> a = x_args<R>(c, field, mode, delta, t_off);
+    c->launches++;
+    ProfScope ps(c, PK_X);
+    SGP_CUDA(c, launch_xyplane(c->n[0], a, (const TwE<R>*)c->tw[1], c->err_dev, c->n[2],
+                                window_members(c), c->stream));
+    return SGP_OK;
+  }
+}
+
+// the x-passes of the steps and substeps (xy-plane passes under variant 5)
 template <typename R>
 sgp_status x_pass(sgp_ctx* c, int mode, double delta, double t_off) {
+  if (plane_pass(c)) return xy_pass_on<R>(c, window_field(c), mode, delta, t_off);
   return x_pass_on<R>(c, window_field(c), mode, delta, t_off);
 }
 
@@ -721,13 +755,16 @@ sgp_status line_pass(sgp_ctx* c, int axis, int mode, const LinTables* t) {
 }
 
 // Linear flow over delta between x-passes.  Entry: x-spectral (the x-pass
-// has done its forward transform).  Exit: x-spectral.
+// has done its forward transform; with xy, x- and y-spectral: the x-passes
+// are xy-plane passes).  Exit: the same.
 template <typename R>
-sgp_status linear_middle_on(sgp_ctx* c, void* f, double delta) {
+sgp_status linear_middle_on(sgp_ctx* c, void* f, double delta, bool xy = false) {
   const LinTables* t = nullptr;
   SGP_TRY(get_tables<R>(c, delta, &t));
   if (c->dim == 2) {
     SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD | LP_MIX | LP_INV, t));
+  } else if (xy) {
+    SGP_TRY(line_pass_on<R>(c, f, 2, LP_FWD | LP_MIX | LP_INV, t));
   } else {
     SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD, nullptr));
     SGP_TRY(line_pass_on<R>(c, f, 2, LP_FWD | LP_MIX | LP_INV, t));
@@ -738,7 +775,7 @@ sgp_status linear_middle_on(sgp_ctx* c, void* f, double delta) {
 
 template <typename R>
 sgp_status linear_middle(sgp_ctx* c, double delta) {
-  return linear_middle_on<R>(c, window_field(c), delta);
+  return linear_middle_on<R>(c, window_field(c), delta, plane_pass(c));
 }
 
 // substep pattern of one step, Sec. 3.3
@@ -875,7 +912,7 @@ sgp_status get_graph(sgp_ctx* c, long long steps, double dt, int scheme, cudaGra
 // Launches issued by one chunk of `steps` steps (for the launch counter):
 // the pass count of emit_steps plus the time update.
 long long chunk_launches(const sgp_ctx* c, long long steps, int scheme) {
-  const long long per_l = c->dim == 2 ? 1 : 3;
+  const long long per_l = (c->dim == 2 || plane_pass(c)) ? 1 : 3;
   long long n = 1;
   bool xspec = false;
   const std::vector<SubRec> subs = merged_substeps(scheme, steps, 1.0);
@@ -1601,14 +1638,25 @@ void drop_graphs(sgp_ctx* c) {
   }
 }
 
+// Does variant v exist for axis a of this context's grid?  Variants 0-4
+// depend on the line length alone; variant 5 is the x-pass variant of 3D
+// FP32 grids with NX = NY = 64 or 128.
+bool axis_variant_ok(const sgp_ctx* c, int a, int v) {
+  if (v == 5) return a == 0 && plane_ok(c);
+  return variant_exists(c->prec == SGP_F32 ? 4 : 8, c->n[a], v);
+}
+
 // Switch axis `a` to variant v: twiddles of its radix plan, kernel
 // attributes; captured graphs are dropped (they embed the old kernels).
 sgp_status use_variant(sgp_ctx* c, int a, int v) {
-  const int pb = c->prec == SGP_F32 ? 4 : 8;
-  if (!variant_exists(pb, c->n[a], v))
+  if (!axis_variant_ok(c, a, v))
     return fail(c, SGP_EINVAL, "variant %d does not exist for N = %d on axis %d", v, c->n[a], a);
   if (v == 4 && !tensor_map_encoder())      // fetched now, not inside a later stream capture
     return fail(c, SGP_EUNSUPPORTED, "the driver has no tensor-map encoder (variant 4)");
+  if (v == 5) {
+    const cudaError_t e = prepare_xyplane(c->n[0]);
+    if (e != cudaSuccess) return fail(c, SGP_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  }
   if (v == 3 && !c->tw4[a]) {
     SGP_CUDA(c, cudaStreamSynchronize(c->stream));
     SGP_CUDA(c, dev_alloc(c, &c->tw4[a], (size_t)c->n[a] * sizeof(TwE<float>)));
@@ -1649,7 +1697,7 @@ std::string tune_key(const sgp_ctx* c) {
 // warm-up step: the data stay a physical state, so the nonlinear flow takes
 // its usual branches, and the pass interplay of a real step is included.  A
 // variant replaces an earlier (lower-numbered) one only when it is at least
-// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][5]:
+// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][6]:
 // ms per step with that variant (-1 where a variant does not exist or the
 // axis is absent).
 template <typename R>
@@ -1665,14 +1713,13 @@ sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int pb = sizeof(R);
   int best[3] = {c->var[0], c->var[1], c->var[2]};
   if (ms_out)
     for (int k = 0; k < 3 * kVariants; ++k) ms_out[k] = -1.0;
   for (int a = 0; a < c->dim && st == SGP_OK; ++a) {
     double best_ms = -1.0;
     for (int v = 0; v < kVariants && st == SGP_OK; ++v) {
-      if (!variant_exists(pb, c->n[a], v)) continue;
+      if (!axis_variant_ok(c, a, v)) continue;
       if (a == 0 && v == 4) continue;     // the x-pass of variant 4 is variant 1
       if (v == 4 && !tensor_map_encoder()) continue;
       st = use_variant(c, a, v);
@@ -2148,9 +2195,8 @@ int sgp_variant_exists(int prec, int n, int variant) {
 sgp_status sgp_set_plan(sgp_ctx* c, const int* variants) {
   if (!c) return SGP_EINVAL;
   if (!variants) return fail(c, SGP_EINVAL, "NULL variants");
-  const int pb = c->prec == SGP_F32 ? 4 : 8;
   for (int a = 0; a < c->dim; ++a)
-    if (!variant_exists(pb, c->n[a], variants[a]))
+    if (!axis_variant_ok(c, a, variants[a]))
       return fail(c, SGP_EINVAL, "variant %d does not exist for N = %d on axis %d", variants[a],
                   c->n[a], a);
   DeviceGuard guard(c->device);

@@ -105,6 +105,48 @@ cudaError_t launch_xpass_v<Real, V>(int N, const XPassArgs<Real>& a, int members
   }
 }
 
+#if SGP_XY_PLANE
+// x-pass variant 5 (FP32): the xy-plane pass of 3D grids with NX = NY = N;
+// compiled with variant 1, whose x-pass serves the variant's other x-passes
+static_assert(sizeof(Real) == 4, "the xy-plane pass is FP32 only");
+
+template <int N>
+static cudaError_t xyplane_prepare_n() {
+  typedef PlCfg<Real, N, elems_per_thread<Real, N>()> Cfg;
+  static int done = -1;
+  return prepare(k_xyplane<Real, N, elems_per_thread<Real, N>()>, Cfg::SMEM, &done);
+}
+
+template <int N>
+static cudaError_t xyplane_n(const XPassArgs<Real>& a, const TwE<Real>* twy, int* err, int planes, int members,
+                             cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef PlCfg<Real, N, E> Cfg;
+  cudaError_t e = xyplane_prepare_n<N>();
+  if (e != cudaSuccess) return e;
+  dim3 grid(Cfg::CS, planes, members);      // the kernel's cluster is (CS, 1, 1)
+  k_xyplane<Real, N, E><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, twy, err);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_xyplane(int N) {
+  switch (N) {
+    case 64: return xyplane_prepare_n<64>();
+    case 128: return xyplane_prepare_n<128>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_xyplane(int N, const XPassArgs<Real>& a, const TwE<Real>* twy, int* err, int planes,
+                           int members, cudaStream_t s) {
+  switch (N) {
+    case 64: return xyplane_n<64>(a, twy, err, planes, members, s);
+    case 128: return xyplane_n<128>(a, twy, err, planes, members, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#endif
+
 #if SGP_VAR == 0
 template <int N>
 static cudaError_t obs_x_n(const ObsXArgs<Real>& a, int members, cudaStream_t s) {

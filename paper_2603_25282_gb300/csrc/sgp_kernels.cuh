@@ -456,6 +456,43 @@ __device__ __forceinline__ C ld_field(const C* p) {
   else return *p;
 }
 
+// The nonlinear flow at the points i + T e of one row that the calling thread
+// holds, staged in the row's exchange buffers b0 + c * bstride: the thread
+// processes exactly the points it staged, so no barrier is needed.  prm: the
+// member's rotation and parameters (cos, sin of Omega t, c0 + c2/5, c1, c2,
+// gx^2/2, gy^2/2, gz^2/2); yz: the row's y and z.
+template <typename R, int N, int E>
+__device__ __forceinline__ void row_flow(cplx<R> (&v)[5][E], const XPassArgs<R>& a, cplx<R>* b0,
+                                         int bstride, int i, const R* prm, const R* yz) {
+  typedef cplx<R> C;
+  constexpr int T = N / E;
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int e = 0; e < E; ++e) b0[c * bstride + i + T * e] = v[c][e];
+  const R co = prm[0], si = prm[1];
+  const R c0p = prm[2], c1 = prm[3], c2 = prm[4];
+  const R gx2h = prm[5], gy2h = prm[6], gz2h = prm[7];
+#pragma unroll 1
+  for (int j = i; j < N; j += T) {
+    const R y = yz[0];
+    const R zz = gz2h * yz[1] * yz[1];
+    const R x = a.x0 + (R)j * a.hx;
+    const R xr = co * x + si * y;
+    const R yr = co * y - si * x;
+    const R V = gx2h * xr * xr + gy2h * yr * yr + zz;
+    C* pp = b0 + j;
+    C p[5] = {pp[0], pp[bstride], pp[2 * bstride], pp[3 * bstride], pp[4 * bstride]};
+    nonlinear_point<R>(p, V, a.delta, c0p, c1, c2);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) pp[c * bstride] = p[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[c][e] = b0[c * bstride + i + T * e];
+}
+
 // Body of the x-pass for block (bx, member): the CTA's rows are
 // bx * ROWS .. bx * ROWS + ROWS - 1 of member `member`.  Called by k_xpass
 // with the block's own coordinates and by the persistent ensemble kernel
@@ -512,32 +549,7 @@ __device__ __forceinline__ void xpass_body(const XPassArgs<R>& a, int bx, int me
   if (a.mode & XP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, bid);
   if (a.mode & XP_NL) {
     group_sync<GT>(bid);              // the row's exchange reads are done
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-#pragma unroll
-      for (int e = 0; e < E; ++e) b0[c * bstride + i + T * e] = v[c][e];
-    // no barrier: the thread processes exactly the points i + T e it staged
-    const R co = s_prm[0], si = s_prm[1];
-    const R c0p = s_prm[2], c1 = s_prm[3], c2 = s_prm[4];
-    const R gx2h = s_prm[5], gy2h = s_prm[6], gz2h = s_prm[7];
-#pragma unroll 1
-    for (int j = i; j < N; j += T) {
-      const R y = s_yz[g][0];
-      const R zz = gz2h * s_yz[g][1] * s_yz[g][1];
-      const R x = a.x0 + (R)j * a.hx;
-      const R xr = co * x + si * y;
-      const R yr = co * y - si * x;
-      const R V = gx2h * xr * xr + gy2h * yr * yr + zz;
-      C* pp = b0 + j;
-      C p[5] = {pp[0], pp[bstride], pp[2 * bstride], pp[3 * bstride], pp[4 * bstride]};
-      nonlinear_point<R>(p, V, a.delta, c0p, c1, c2);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) pp[c * bstride] = p[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-#pragma unroll
-      for (int e = 0; e < E; ++e) v[c][e] = b0[c * bstride + i + T * e];
+    row_flow<R, N, E>(v, a, b0, bstride, i, s_prm, s_yz[g]);
   }
   if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, bid);
   if (valid) {
@@ -746,6 +758,222 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 // limit of a tile-load wait: about a second at the GPU's clock
 constexpr long long kTmaWaitCycles = 2000000000LL;
+
+// ----------------------------------------------------------------------------
+// xy-plane pass (3D, FP32, NX = NY = N): one thread-block cluster per z plane
+// ----------------------------------------------------------------------------
+// The x-pass and the two y-line passes of a 3D step fused: a cluster of
+// CS = N / L CTAs holds one z plane of one member, CTA r owning the rows
+// y = r L .. r L + L - 1 (row phase) and the columns x = r L .. r L + L - 1
+// (column phase).  With XP_INV the plane comes in by columns, takes the
+// inverse y transform and is handed to the row owners; the rows take the
+// inverse x transform, the nonlinear flow and the forward x transform; with
+// XP_FWD they are handed back to the column owners for the forward y
+// transform and leave by columns.  A hand-over is a set of asynchronous
+// stores into the other CTAs' shared memory (distributed shared memory),
+// each counting its bytes on an mbarrier of the receiving CTA, which waits
+// for all of them (a bounded wait: past the limit the error word is set);
+// a cluster barrier before it makes sure every CTA is done with the buffers
+// the stores land in.
+// The field is then y- and x-spectral between passes, so a step needs only
+// this pass and the z-line pass.  Every line takes exactly the arithmetic of
+// the x-pass and the y-line pass with the same elements per thread, so the
+// results equal those of the unfused passes bit for bit.
+template <typename R, int N, int E>
+struct PlCfg {
+  static constexpr int T = N / E;             // threads per line
+  static constexpr int L = 16;                // lines per CTA in either phase
+  static constexpr int CS = N / L;            // CTAs per cluster
+  static constexpr int THREADS = L * T;
+  static constexpr int MINB = 512 / THREADS;  // 16 warps per SM
+  static constexpr int LP = line_pad<R>(N);   // row exchange buffers (x-pass layout)
+  static constexpr int RSTR = L * LP;         // row phase: component stride
+  static constexpr int CP = line_pad_tile<R>(N, L);   // column exchange buffers (line-pass layout)
+  static constexpr int CSTR = L * CP;         // column phase: buffer stride (two buffers)
+  static constexpr int SL = 5 * N * L;        // column-layout slice [c][y][x - r L]
+  static constexpr int REG = (5 * RSTR > SL ? 5 * RSTR : SL) > 2 * CSTR ? (5 * RSTR > SL ? 5 * RSTR : SL)
+                                                                        : 2 * CSTR;
+  static constexpr size_t SMEM = 2 * sizeof(TwE<R>) * (size_t)N + sizeof(cplx<R>) * (size_t)REG;
+  static_assert(N % L == 0 && L % T == 0 && CS >= 2 && CS <= 8, "xy-plane pass geometry");
+  static_assert(MINB * SMEM <= 227 * 1024, "xy-plane pass shared memory");
+};
+
+// thread-block clusters: the two halves of a barrier over the cluster
+// (release / acquire: this CTA's shared-memory accesses before the arrive
+// are performed before the other CTAs pass their wait), the address of a
+// shared-memory location in another CTA of the cluster, an asynchronous
+// store there that counts its bytes on an mbarrier of that CTA, and a
+// bounded wait on a local mbarrier that such stores complete (acquire at
+// cluster scope: the stored data are visible after it)
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_map(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async(unsigned addr, float2 v, unsigned bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(unsigned long long* b, unsigned parity, long long max_cycles) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait_cluster(b, parity))
+    if (clock64() - t0 > max_cycles) return false;
+  return true;
+}
+
+template <typename R, int N, int E>
+__global__ void __cluster_dims__(PlCfg<R, N, E>::CS, 1, 1)
+    __launch_bounds__(PlCfg<R, N, E>::THREADS, PlCfg<R, N, E>::MINB)
+k_xyplane(XPassArgs<R> a, const TwE<R>* __restrict__ twy_g, int* err) {
+  typedef cplx<R> C;
+  typedef PlCfg<R, N, E> Cfg;
+  constexpr int T = Cfg::T, L = Cfg::L;
+  // bytes a CTA receives in one hand-over: L lines of N elements, five components
+  constexpr unsigned XBYTES = 5u * L * N * sizeof(C);
+  static_assert(sizeof(R) == 4, "xy-plane pass: FP32");
+  extern __shared__ __align__(16) unsigned char smem_pl[];
+  TwE<R>* twx = reinterpret_cast<TwE<R>*>(smem_pl);
+  TwE<R>* twy = twx + N;
+  C* X = reinterpret_cast<C*>(twy + N);
+  __shared__ R s_prm[8];
+  __shared__ R s_yz[L][2];
+  // completion of the two hand-overs into this CTA (rows, then columns)
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  const int r = blockIdx.x;                  // rank in the cluster (gridDim.x = CS)
+  const int plane = blockIdx.y;
+  const int member = blockIdx.z;
+  const bool inv = a.mode & XP_INV, fwd = a.mode & XP_FWD;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_fence_init();
+    if (inv) mbar_expect_tx(&s_bar[0], XBYTES);
+    if (fwd) mbar_expect_tx(&s_bar[1], XBYTES);
+  }
+  for (int k = threadIdx.x; k < N; k += Cfg::THREADS) {
+    twx[k] = a.tw[k];
+    twy[k] = twy_g[k];
+  }
+  if ((a.mode & XP_NL) && threadIdx.x == 0) {
+    const MemberPrm& P = a.mp[member];
+    const double t = *a.t_base + a.t_off;
+    double sn, cs;
+    sincos(P.omega * t, &sn, &cs);
+    s_prm[0] = (R)cs;
+    s_prm[1] = (R)sn;
+    s_prm[2] = (R)(P.c0 + P.c2 / 5.0);
+    s_prm[3] = (R)P.c1;
+    s_prm[4] = (R)P.c2;
+    s_prm[5] = (R)P.gx2h;
+    s_prm[6] = (R)P.gy2h;
+    s_prm[7] = (R)P.gz2h;
+  }
+  if ((a.mode & XP_NL) && threadIdx.x < L) {
+    s_yz[threadIdx.x][0] = a.y0 + (R)(r * L + threadIdx.x) * a.hy;
+    s_yz[threadIdx.x][1] = a.z0 + (R)plane * a.hz;
+  }
+  C* fm = a.field + (size_t)member * 5 * a.ntot + (size_t)plane * N * N;
+  // row phase: row g (y = r L + g), thread i of the row holds x = i + T e
+  const int g = threadIdx.x / T;
+  const int i = threadIdx.x - g * T;
+  C* rb0 = X + g * Cfg::LP;
+  // column phase: column cl (x = r L + cl), thread ic of the column holds y = ic + T e
+  const int cl = threadIdx.x % L;
+  const int ic = threadIdx.x / L;
+  C* cb0 = X + cl * Cfg::CP;
+  C v[5][E];
+  if (inv) {
+    const C* src = fm + (size_t)ic * N + r * L + cl;
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = src[(size_t)c * a.ntot + (size_t)T * e * N];
+    __syncthreads();                         // tables, s_prm, s_yz, mbarriers
+    fft_lines<R, N, E, +1, 5, 2>(v, ic, twy, cb0, Cfg::CSTR);
+    // every CTA is done with its exchange buffers, and every CTA's mbarriers
+    // are initialised
+    cluster_arrive();
+    cluster_wait();
+    // y = ic + T e goes to row (ic + T e) % L of CTA (ic + T e) / L = T e / L
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int y = ic + T * e;
+      const unsigned rank = (unsigned)(T * e / L);
+      const unsigned dst = cluster_map(X, rank) + (unsigned)(((y % L) * Cfg::LP + r * L + cl) * sizeof(C));
+      const unsigned bar = cluster_map(&s_bar[0], rank);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) st_async(dst + (unsigned)(c * Cfg::RSTR * sizeof(C)), v[c][e], bar);
+    }
+    if (!mbar_wait_cluster(&s_bar[0], 0, kTmaWaitCycles) && err) atomicExch(err, 1);
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = rb0[c * Cfg::RSTR + i + T * e];
+    fft_lines<R, N, E, +1, 5, 5>(v, i, twx, rb0, Cfg::RSTR);
+  } else {
+    const C* src = fm + (size_t)(r * L + g) * N + i;
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = src[(size_t)c * a.ntot + T * e];
+    __syncthreads();                         // tables, s_prm, s_yz, mbarriers
+  }
+  if (a.mode & XP_NL) {
+    __syncthreads();                         // the rows' exchange reads are done
+    row_flow<R, N, E>(v, a, rb0, Cfg::RSTR, i, s_prm, s_yz[g]);
+  }
+  if (fwd) {
+    // the forward x transform reads and writes the row buffers; the other
+    // CTAs may store into them once every CTA has arrived after it
+    fft_lines<R, N, E, -1, 5, 5>(v, i, twx, rb0, Cfg::RSTR);
+    cluster_arrive();
+    cluster_wait();
+    // x = i + T e goes to column x % L of CTA x / L = T e / L (column layout)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int x = i + T * e;
+      const unsigned rank = (unsigned)(T * e / L);
+      const unsigned dst = cluster_map(X, rank) + (unsigned)(((r * L + g) * L + x % L) * sizeof(C));
+      const unsigned bar = cluster_map(&s_bar[1], rank);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) st_async(dst + (unsigned)(c * N * L * sizeof(C)), v[c][e], bar);
+    }
+    if (!mbar_wait_cluster(&s_bar[1], 0, kTmaWaitCycles) && err) atomicExch(err, 1);
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = X[c * N * L + (ic + T * e) * L + cl];
+    fft_lines<R, N, E, -1, 5, 2>(v, ic, twy, cb0, Cfg::CSTR);
+    C* dst = fm + (size_t)ic * N + r * L + cl;
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) dst[(size_t)c * a.ntot + (size_t)T * e * N] = v[c][e];
+  } else {
+    C* dst = fm + (size_t)(r * L + g) * N + i;
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) dst[(size_t)c * a.ntot + T * e] = v[c][e];
+  }
+}
 
 // Body of the line pass for block (bx, plane, member): the CTA's columns
 // are bx * TILE .. bx * TILE + TILE - 1 of plane `plane` (the z slice for

@@ -44,7 +44,11 @@ inline bool supported_n(int n) {
 //      registers of field data)
 //   4  FP32 only.  Line pass: geometry 1 with the tile loaded by tensor
 //      copies (TMA) into shared memory; x-pass: the same as variant 1
-constexpr int kVariants = 5;
+//   5  FP32, x-pass of 3D grids with NX = NY = 64 or 128 only: the steps'
+//      x-passes become xy-plane passes (k_xyplane: one thread-block cluster
+//      per z plane, the y transforms done there), so a step drops its
+//      y-line passes; x-passes outside the steps are those of variant 1
+constexpr int kVariants = 6;
 
 template <typename R, int N, int V>
 constexpr int variant_elems() {
@@ -53,14 +57,14 @@ constexpr int variant_elems() {
 // geometry of variant V for the x-pass (PART 0) and the line pass (PART 1)
 template <int N, int V, int PART>
 constexpr int variant_geom() {
-  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : V == 4 ? 1 : V;
+  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : (V == 4 || V == 5) ? 1 : V;
 }
 
 // Does variant V exist for line length N (prec_bytes 4 or 8)?
 inline bool variant_exists(int prec_bytes, int N, int V) {
   if (!supported_n(N) || V < 0 || V >= kVariants) return false;
   if (V == 3 || V == 4) return prec_bytes == 4;
-  return true;
+  return V != 5;       // variant 5 depends on the whole grid (plane_ok in the host runtime)
 }
 // Elements per thread of variant V (the twiddle table layout depends on it).
 inline int variant_elems_rt(int prec_bytes, int N, int V) {
@@ -90,8 +94,15 @@ cudaError_t launch_linepass_tma(int N, const LPassArgs<float>& a, const CUtensor
                                 int members, cudaStream_t s);
 cudaError_t prepare_linepass_tma(int N);
 PassGeom linepass_geom_tma(int N);
+// Variant 5 of the x-pass: the xy-plane pass over `planes` z planes of
+// `members` members (N = NX = NY; twy: the y twiddles; err: the word a
+// bounded wait for a hand-over sets when it gives up).
+cudaError_t launch_xyplane(int N, const XPassArgs<float>& a, const TwE<float>* twy, int* err, int planes,
+                           int members, cudaStream_t s);
+cudaError_t prepare_xyplane(int N);
 
-// x-pass variant 4 is variant 1; the line pass has its own
+// x-pass variants 4 and 5 are variant 1 (variant 5's plane pass has its own
+// entry point); the line pass has its own variant 4
 #define SGP_VARIANT_SWITCH_X(V, CALL, FAIL)                  \
   switch (V) {                                               \
     case 0: return CALL(0);                                  \
@@ -101,6 +112,7 @@ PassGeom linepass_geom_tma(int N);
       if constexpr (sizeof(R) == 4) return CALL(3);          \
       return FAIL;                                           \
     case 4:                                                  \
+    case 5:                                                  \
       if constexpr (sizeof(R) == 4) return CALL(1);          \
       return FAIL;                                           \
     default: return FAIL;                                    \

@@ -25,6 +25,7 @@ def test_algorithmic_bytes_per_point_step(bench):
     assert bench.bytes_per_point_step(2, "ts4", "f32") == (480, 80)
     assert bench.bytes_per_point_step(3, "ts2", "f32") == (320, 80)
     assert bench.bytes_per_point_step(3, "ts4", "f32") == (960, 80)
+    assert bench.bytes_per_point_step(3, "ts2", "f32", (5, 1, 1)) == (160, 80)   # xy-plane pass
     assert bench.bytes_per_point_step(2, "ts2", "f64") == (320, 160)
 
 

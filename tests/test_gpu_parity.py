@@ -178,7 +178,8 @@ def test_f32_ts4_full_size_first_steps():
     ref, _ = _oracle_run(n, L, prm, psi, 2, 5e-4, "ts4")
     out64, _ = _gpu_run(n, L, prm, psi, 2, 5e-4, "ts4", "f64")
     assert O.rel_l2(out64, ref) < 1e-10
-    for plan in [(vx, vy) for vx in range(sgp.N_VARIANTS) for vy in range(sgp.N_VARIANTS)]:
+    vs = [v for v in range(sgp.N_VARIANTS) if sgp.variant_exists("f32", 512, v)]
+    for plan in [(vx, vy) for vx in vs for vy in vs]:
         c = _ctx(n, L, "f32", **prm)
         c.set_plan(plan)
         c.set_state(psi[None].astype(np.complex64).copy(), 0.0)
@@ -386,7 +387,7 @@ def test_3d_128_full_size_first_steps():
         assert O.rel_l2(out64, ref) < 1e-10, scheme
         for v in range(sgp.N_VARIANTS):          # every plan the autotuner tries per axis
             c = _ctx(n, L, "f32", **prm)
-            c.set_plan((v, v, v))
+            c.set_plan((v, v, v) if v != 5 else (5, 1, 1))   # variant 5: the xy-plane pass
             c.set_state(psi[None].astype(np.complex64).copy(), 0.0)
             c.step(2, 1e-3, scheme)
             out32 = c.get_state()[0].astype(np.complex128)
