@@ -25,7 +25,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.
 # (object name, source, extra defines)
 UNITS = [
     ("api", "sgp_api.cu", []),
-    ("adjoint", "sgp_adjoint.cu", []),
+    ("adjoint_flo", "sgp_adjoint.cu", ["-DSGP_REAL=float", "-DSGP_REDUCE_PARAMS=1"]),
+    ("adjoint_dou", "sgp_adjoint.cu", ["-DSGP_REAL=double"]),
     ("lab", "sgp_lab.cu", []),
     ("persist_flo", "sgp_persist.cu", ["-DSGP_REAL=float", "-DSGP_PERSIST_DEFINE_SUPPORTED=1"]),
     ("persist_dou", "sgp_persist.cu", ["-DSGP_REAL=double"]),

@@ -1115,25 +1115,29 @@ sgp_status record_steps(sgp_ctx* c, long long nsteps, double dt, int scheme, lon
   return SGP_OK;
 }
 
-// physical space -> unnormalised full transform (all axes)
+// Rows of the parameter partials per member: one per CTA of the adjoint
+// x-pass, then one per CTA of the line pass that holds the full transform
+// (y lines in 2D, z lines in 3D).
 template <typename R>
-sgp_status to_spectral(sgp_ctx* c, void* f) {
-  SGP_TRY(x_pass_on<R>(c, f, XP_FWD, 0.0, 0.0));
-  SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD, nullptr));
-  if (c->dim == 3) SGP_TRY(line_pass_on<R>(c, f, 2, LP_FWD, nullptr));
-  return SGP_OK;
+int adjoint_prows(const sgp_ctx* c) {
+  const int axis = c->dim == 2 ? 1 : 2;
+  const int planes = c->dim == 2 ? c->n[2] : c->n[1];
+  return xadj_ctas<R>(c->n[0], c->n[1] * c->n[2]) + linepass_adj_tiles<R>(c->n[axis], c->n[0]) * planes;
 }
 
-// g <- (D N_d(Phi_in))^T g at Phi_out = phi, plus the parameter terms (added
-// to the per-block partials)
+// g <- (D N_d(Phi_in))^T g at Phi_out = phi (physical space), plus the
+// parameter terms; with XP_INV g comes in x-spectral (the inverse
+// x-transform first), with XP_FWD it leaves x-spectral
 template <typename R>
-sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t_off) {
-  NLAdjArgs<R> a{};
+sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t_off, int mode) {
+  XAdjArgs<R> a{};
   a.g = (cplx<R>*)c->adj.g;
   a.phi = (const cplx<R>*)phi;
+  a.tw = (const TwE<R>*)c->tw[0];
   a.ntot = c->ntot;
-  a.nx = c->n[0];
+  a.rows = c->n[1] * c->n[2];
   a.ny = c->n[1];
+  a.mode = mode;
   a.x0 = -c->L[0];
   a.hx = c->h[0];
   a.y0 = -c->L[1];
@@ -1145,52 +1149,80 @@ sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t
   a.t_off = t_off;
   a.mp = c->mp_dev;
   a.partials = c->adj.part;
-  a.nblocks = adjoint_blocks(c->ntot);
+  a.prows = adjoint_prows<R>(c);
   c->launches++;
-  ProfScope ps(c, PK_OTHER);
-  SGP_CUDA(c, launch_nl_adjoint<R>(a, c->batch, c->stream));
+  ProfScope ps(c, PK_X);
+  SGP_CUDA(c, launch_xadj<R>(c->n[0], a, c->batch, c->stream));
   return SGP_OK;
 }
 
-// g <- L(-d) g, and the Omega and gamma terms from the transforms of g and
-// of Phi_out (phi_spec: that transform made already, else made here)
+// The linear flow over delta on the x-spectral field f through the line
+// pass of a gradient (in 3D between the y-line transforms), the field left
+// x-spectral.  h: its hooks (the parameter terms of the sweep or the copy
+// of the recomputation).
 template <typename R>
-sgp_status adjoint_linear(sgp_ctx* c, const void* phi, double delta, const void* phi_spec = nullptr) {
-  AdjRec& r = c->adj;
-  if (!phi_spec) {
-    SGP_CUDA(c, cudaMemcpyAsync(r.spec, phi, state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-    SGP_TRY(to_spectral<R>(c, r.spec));
-    phi_spec = r.spec;
-  }
-  SGP_TRY(to_spectral<R>(c, r.g));
-  LinParArgs<R> a{};
-  a.g = (const cplx<R>*)r.g;
-  a.s = (const cplx<R>*)phi_spec;
+sgp_status linear_hooked(sgp_ctx* c, void* f, double delta, const AdjHook<R>& h) {
+  const LinTables* t = nullptr;
+  SGP_TRY(get_tables<R>(c, delta, &t));
+  const int axis = c->dim == 2 ? 1 : 2;
+  if (c->dim == 3) SGP_TRY(line_pass_on<R>(c, f, 1, LP_FWD, nullptr));
+  LPassArgs<R> a{};
+  a.field = (cplx<R>*)f;
+  a.tw = (const TwE<R>*)c->tw[axis];
   a.ntot = c->ntot;
+  a.nx = c->n[0];
+  const long long nxy = (long long)c->n[0] * c->n[1];
+  int planes;
+  if (axis == 1) {
+    a.line_stride = c->n[0];
+    a.plane_stride = nxy;
+    planes = c->n[2];
+  } else {
+    a.line_stride = nxy;
+    a.plane_stride = c->n[0];
+    planes = c->n[1];
+  }
+  a.mode = LP_FWD | LP_MIX | LP_INV;
+  a.axis = axis;
   a.NX = c->n[0];
   a.NY = c->n[1];
-  a.Lx = c->L[0];
-  a.Ly = c->L[1];
-  a.delta = delta;
-  a.scale = 1.0 / (double)c->ntot;
-  a.mp = c->mp_dev;
-  a.partials = r.part;
-  a.nblocks = adjoint_blocks(c->ntot);
+  a.mt_member = c->shared_lin ? 0 : (long long)(c->n[0] / 2 + 1) * (c->n[1] / 2 + 1) * MT_STRIDE;
+  a.mt = (const R*)t->mt;
+  a.kz = (const cplx<R>*)t->kz;
+  {
+    const double inv = 1.0 / ((double)c->n[0] * c->n[1] * (c->dim == 3 ? c->n[2] : 1));
+    a.inv_hi = (R)inv;
+    a.inv_lo = (R)(inv - (double)a.inv_hi);
+  }
+  a.err = c->err_dev;
   c->launches++;
   {
-    ProfScope ps(c, PK_OTHER);
-    SGP_CUDA(c, launch_lin_param<R>(a, c->batch, c->stream));
+    ProfScope ps(c, axis == 1 ? PK_Y : PK_Z);
+    SGP_CUDA(c, launch_linepass_adj<R>(c->n[axis], a, h, planes, c->batch, c->stream));
   }
-  // the linear flow over -delta on the transformed g, then back to space
-  const LinTables* t = nullptr;
-  SGP_TRY(get_tables<R>(c, -delta, &t));
-  if (c->dim == 2) {
-    SGP_TRY(line_pass_on<R>(c, r.g, 1, LP_MIX | LP_INV, t));
-  } else {
-    SGP_TRY(line_pass_on<R>(c, r.g, 2, LP_MIX | LP_INV, t));
-    SGP_TRY(line_pass_on<R>(c, r.g, 1, LP_INV, nullptr));
-  }
-  return x_pass_on<R>(c, r.g, XP_INV, 0.0, 0.0);
+  if (c->dim == 3) SGP_TRY(line_pass_on<R>(c, f, 1, LP_INV, nullptr));
+  return SGP_OK;
+}
+
+// g <- L(-d) g on the x-spectral g, with the Omega and gamma terms of every
+// mode; phi_tap: the recomputation's copy of the substep's output after the
+// mix (its full transform divided by the number of grid points, so the
+// products of the two transforms sum over the grid with scale 1)
+template <typename R>
+sgp_status adjoint_linear(sgp_ctx* c, double delta, const void* phi_tap) {
+  AdjHook<R> h{};
+  h.spec = (const cplx<R>*)phi_tap;
+  h.mp = c->mp_dev;
+  h.partials = c->adj.part;
+  h.prows = adjoint_prows<R>(c);
+  h.prow0 = xadj_ctas<R>(c->n[0], c->n[1] * c->n[2]);
+  const int axis = c->dim == 2 ? 1 : 2;
+  h.tiles = linepass_adj_tiles<R>(c->n[axis], c->n[0]);
+  h.Lx = c->L[0];
+  h.Ly = c->L[1];
+  h.delta = delta;
+  h.scale = 1.0;
+  return linear_hooked<R>(c, c->adj.g, -delta, h);
 }
 
 // Substeps of a recomputed segment of n steps (times relative to its start).
@@ -1198,59 +1230,76 @@ std::vector<SubRec> segment_substeps(int scheme, long long n, double dt) {
   return merged_substeps(scheme, n, dt);
 }
 
-// The states of a segment recomputed from seg[0] substep by substep (the
-// segment start time from the device clock).  With spec (the pipelined
-// sweep), the transform of every linear substep's output goes there too
-// (one state per linear substep, in order), for the parameter terms of the
-// adjoint sweep.
+// The states of a segment recomputed from seg[0] (the segment's start) with
+// the passes of the forward steps, working in place on seg[0]: the output
+// of nonlinear substep j is copied to seg[j + 1] (physical space) by the
+// x-pass after its flow, and the output of the k-th linear substep, after
+// the mix, to spec[k] (its transform over the number of grid points) by
+// the line pass.  Times relative to the segment start on the device clock.
 template <typename R>
-sgp_status emit_recompute(sgp_ctx* c, const std::vector<SubRec>& subs, char* seg, char* spec = nullptr) {
+sgp_status emit_recompute(sgp_ctx* c, const std::vector<SubRec>& subs, char* seg, char* spec) {
   const size_t sb = state_bytes(c);
   size_t nl = 0;
+  bool xspec = false;
   for (size_t j = 0; j < subs.size(); ++j) {
-    void* out = seg + sb * (j + 1);
-    SGP_CUDA(c, cudaMemcpyAsync(out, seg + sb * j, sb, cudaMemcpyDeviceToDevice, c->stream));
     if (subs[j].kind == 'N') {
-      SGP_TRY(x_pass_on<R>(c, out, XP_NL, subs[j].delta, subs[j].toff));
+      int mode = XP_NL | (xspec ? XP_INV : 0);
+      xspec = (j + 1 < subs.size());
+      if (xspec) mode |= XP_FWD;
+      XPassArgs<R> a = x_args<R>(c, seg, mode, subs[j].delta, subs[j].toff);
+      a.tw = (const TwE<R>*)c->tw[0];
+      a.tap = (cplx<R>*)(seg + sb * (j + 1));
+      c->launches++;
+      ProfScope ps(c, PK_X);
+      SGP_CUDA(c, launch_xpass_tap<R>(c->n[0], a, c->batch, c->stream));
     } else {
-      SGP_TRY(x_pass_on<R>(c, out, XP_FWD, 0.0, 0.0));
-      SGP_TRY(linear_middle_on<R>(c, out, subs[j].delta));
-      SGP_TRY(x_pass_on<R>(c, out, XP_INV, 0.0, 0.0));
-      if (spec) {
-        char* sp = spec + sb * nl++;
-        SGP_CUDA(c, cudaMemcpyAsync(sp, out, sb, cudaMemcpyDeviceToDevice, c->stream));
-        SGP_TRY(to_spectral<R>(c, sp));
-      }
+      if (!xspec) SGP_TRY(x_pass_on<R>(c, seg, XP_FWD, 0.0, 0.0));
+      xspec = true;
+      AdjHook<R> h{};
+      h.tap = (cplx<R>*)(spec + sb * nl++);
+      SGP_TRY(linear_hooked<R>(c, seg, subs[j].delta, h));
     }
   }
   return SGP_OK;
 }
 
-// g carried back through a recomputed segment's substeps in reverse order
-// (spec: the transforms the recomputation made, or null).
+// g carried back through a recomputed segment's substeps in reverse order.
+// g stays x-spectral between a linear substep and the nonlinear one before
+// it, as the field does between the forward passes: a nonlinear substep is
+// one adjoint x-pass (the inverse x-transform of the linear substep after
+// it and the forward x-transform of the one before it fused in), a linear
+// substep one line pass of a gradient (2D; in 3D with the two y-line
+// passes).  g is physical at the segment's ends.
 template <typename R>
-sgp_status emit_adjoint(sgp_ctx* c, const std::vector<SubRec>& subs, const char* seg,
-                        const char* spec = nullptr) {
+sgp_status emit_adjoint(sgp_ctx* c, const std::vector<SubRec>& subs, const char* seg, const char* spec) {
+  AdjRec& r = c->adj;
   const size_t sb = state_bytes(c);
   size_t nl = 0;
   for (const SubRec& q : subs) nl += q.kind == 'L';
+  bool xspec = false;
   for (size_t j = subs.size(); j-- > 0;) {
-    const void* phi_out = seg + sb * (j + 1);
     if (subs[j].kind == 'N') {
-      SGP_TRY(adjoint_nonlinear<R>(c, phi_out, subs[j].delta, subs[j].toff));
+      int mode = xspec ? XP_INV : 0;
+      if (j > 0 && subs[j - 1].kind == 'L') mode |= XP_FWD;
+      SGP_TRY(adjoint_nonlinear<R>(c, seg + sb * (j + 1), subs[j].delta, subs[j].toff, mode));
+      xspec = (mode & XP_FWD) != 0;
     } else {
-      --nl;
-      SGP_TRY(adjoint_linear<R>(c, phi_out, subs[j].delta, spec ? spec + sb * nl : nullptr));
+      if (!xspec) SGP_TRY(x_pass_on<R>(c, r.g, XP_FWD, 0.0, 0.0));
+      SGP_TRY(adjoint_linear<R>(c, subs[j].delta, spec + sb * --nl));
+      xspec = true;
     }
   }
+  if (xspec) SGP_TRY(x_pass_on<R>(c, r.g, XP_INV, 0.0, 0.0));
   return SGP_OK;
 }
 
-// One segment: the recomputation, then the adjoint sweep through it.
+// One segment: the recomputation, then the adjoint sweep through it (the
+// linear substeps' copies spec_off bytes into the segment buffer).
 template <typename R>
-sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs) {
-  SGP_TRY(emit_recompute<R>(c, subs, (char*)c->adj.seg));
-  return emit_adjoint<R>(c, subs, (const char*)c->adj.seg);
+sgp_status emit_segment(sgp_ctx* c, const std::vector<SubRec>& subs, size_t spec_off) {
+  char* seg = (char*)c->adj.seg;
+  SGP_TRY(emit_recompute<R>(c, subs, seg, seg + spec_off));
+  return emit_adjoint<R>(c, subs, seg, seg + spec_off);
 }
 
 void free_adj_graph(sgp_ctx* c) {
@@ -1261,7 +1310,7 @@ void free_adj_graph(sgp_ctx* c) {
 // Captured full-length segment (cached; rebuilt when the run, the buffers or
 // the tables change).
 template <typename R>
-sgp_status segment_graph(sgp_ctx* c, const std::vector<SubRec>& subs, cudaGraphExec_t* out) {
+sgp_status segment_graph(sgp_ctx* c, const std::vector<SubRec>& subs, size_t spec_off, cudaGraphExec_t* out) {
   AdjRec& r = c->adj;
   const void* key[5] = {r.seg, r.g, r.spec, r.part, c->t_dev};
   if (r.graph && r.graph_len == r.interval && r.graph_dt == r.dt &&
@@ -1272,7 +1321,7 @@ sgp_status segment_graph(sgp_ctx* c, const std::vector<SubRec>& subs, cudaGraphE
   free_adj_graph(c);
   const long long launches0 = c->launches;
   SGP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  sgp_status st = emit_segment<R>(c, subs);
+  sgp_status st = emit_segment<R>(c, subs, spec_off);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   r.graph_launches = c->launches - launches0;
@@ -1357,7 +1406,7 @@ sgp_status backward_sweep_pipelined(sgp_ctx* c, const std::vector<SubRec>& full,
   for (cudaEvent_t& e : r.ev)
     if (!e) SGP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   char* segs[2] = {(char*)r.seg, (char*)r.seg2};
-  char* specs[2] = {segs[0] + spec_off, segs[1] + spec_off};   // the linear substeps' transforms
+  char* specs[2] = {segs[0] + spec_off, segs[1] + spec_off};   // the linear substeps' copies
   const bool graphs = c->use_graphs && !c->profiling;
   // the recomputations start after the work already on the context stream
   SGP_CUDA(c, cudaEventRecord(r.ev[0], c->stream));
@@ -1425,10 +1474,15 @@ sgp_status backward_sweep(sgp_ctx* c) {
   AdjRec& r = c->adj;
   const size_t sb = state_bytes(c);
   const auto seq = scheme_seq(r.scheme);
+  // a segment buffer: the start state (the recomputation's working state),
+  // one slot per substep (the nonlinear substeps' outputs), then the copies
+  // of the linear substeps' outputs after the mix
   const size_t per_seg = (size_t)r.interval * seq.size() + 1;
-  SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, sb * per_seg));
-  SGP_TRY(ensure_buf(c, &r.spec, &r.spec_cap, sb));
-  const int nblocks = adjoint_blocks(c->ntot);
+  size_t nlin = 0;
+  for (const auto& q : seq) nlin += q.first == 'L';
+  const size_t seg_bytes = sb * (per_seg + (size_t)r.interval * nlin);
+  SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, seg_bytes));
+  const int nblocks = adjoint_prows<R>(c);
   const size_t part_bytes = (size_t)c->batch * nblocks * GP_N * sizeof(double);
   SGP_TRY(ensure_buf(c, (void**)&r.part, &r.part_cap, part_bytes));
   SGP_CUDA(c, cudaMemsetAsync(r.part, 0, part_bytes, c->stream));
@@ -1439,11 +1493,8 @@ sgp_status backward_sweep(sgp_ctx* c) {
       SGP_TRY(get_tables<R>(c, -st.delta, &t));
     }
   const std::vector<SubRec> full = segment_substeps(r.scheme, r.interval, r.dt);
-  // the pipelined sweep: two segment buffers, each with room for the
-  // transforms of the segment's linear substeps, if the memory is there
-  size_t nlin = 0;
-  for (const auto& q : seq) nlin += q.first == 'L';
-  const size_t pipe_bytes = sb * (per_seg + (size_t)r.interval * nlin);
+  // the pipelined sweep: two segment buffers, if the memory is there
+  const size_t pipe_bytes = seg_bytes;
   bool pipe = r.nck > 1;
   for (int k = 0; k < 2 && pipe; ++k) {
     void** p = k ? &r.seg2 : &r.seg;
@@ -1461,7 +1512,7 @@ sgp_status backward_sweep(sgp_ctx* c) {
       pipe = false;
     }
   }
-  if (!pipe) SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, sb * per_seg));
+  if (!pipe) SGP_TRY(ensure_buf(c, &r.seg, &r.seg_cap, seg_bytes));
   if (pipe) {
     SGP_TRY(backward_sweep_pipelined<R>(c, full, sb * per_seg));
     c->launches++;
@@ -1479,11 +1530,11 @@ sgp_status backward_sweep(sgp_ctx* c) {
                                 cudaMemcpyDeviceToDevice, c->stream));
     if (n == r.interval && graphs && r.nck > 1) {
       cudaGraphExec_t exec = nullptr;
-      SGP_TRY(segment_graph<R>(c, full, &exec));
+      SGP_TRY(segment_graph<R>(c, full, sb * per_seg, &exec));
       SGP_CUDA(c, cudaGraphLaunch(exec, c->stream));
       c->launches += r.graph_launches;
     } else {
-      SGP_TRY(emit_segment<R>(c, n == r.interval ? full : segment_substeps(r.scheme, n, r.dt)));
+      SGP_TRY(emit_segment<R>(c, n == r.interval ? full : segment_substeps(r.scheme, n, r.dt), sb * per_seg));
     }
   }
   c->launches++;

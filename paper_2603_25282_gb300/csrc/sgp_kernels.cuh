@@ -53,6 +53,9 @@ struct XPassArgs {
   const MemberPrm* mp;           // [batch]
   const double* t_base;
   double t_off;
+  // the copy of the rows right after the nonlinear flow (physical space,
+  // same layout as the field) that the x-pass's TAP form writes
+  cplx<R>* tap;
 };
 
 template <typename R>
@@ -497,7 +500,7 @@ __device__ __forceinline__ void row_flow(cplx<R> (&v)[5][E], const XPassArgs<R>&
 // bx * ROWS .. bx * ROWS + ROWS - 1 of member `member`.  Called by k_xpass
 // with the block's own coordinates and by the persistent ensemble kernel
 // for each work item it takes.
-template <typename R, int N, int E, int G, bool CG = false>
+template <typename R, int N, int E, int G, bool CG = false, bool TAP = false>
 __device__ __forceinline__ void xpass_body(const XPassArgs<R>& a, int bx, int member,
                                            unsigned char* smem_raw) {
   typedef cplx<R> C;
@@ -550,6 +553,15 @@ __device__ __forceinline__ void xpass_body(const XPassArgs<R>& a, int bx, int me
   if (a.mode & XP_NL) {
     group_sync<GT>(bid);              // the row's exchange reads are done
     row_flow<R, N, E>(v, a, b0, bstride, i, s_prm, s_yz[g]);
+    if constexpr (TAP) {
+      if (valid) {
+        C* tp = a.tap + (base - a.field);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+#pragma unroll
+          for (int e = 0; e < E; ++e) tp[(size_t)c * a.ntot + T * e] = v[c][e];
+      }
+    }
   }
   if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, bid);
   if (valid) {
@@ -979,10 +991,23 @@ k_xyplane(XPassArgs<R> a, const TwE<R>* __restrict__ twy_g, int* err) {
 // are bx * TILE .. bx * TILE + TILE - 1 of plane `plane` (the z slice for
 // y-lines, the y row for z-lines) of member `member`.  Called by k_linepass
 // with the block's own coordinates and by the persistent ensemble kernel.
-template <typename R, int N, int E, int G, bool CG = false, bool TMA = false>
+// A line pass's hooks after its forward transform and after its mix: the
+// adjoint sweep's line pass adds the per-mode parameter terms of the linear
+// flow after the forward transform (the tile then holds the full transform
+// of g), and the recomputation keeps a copy of the tile after the mix.  The
+// forward passes take NoHook.
+struct NoHook {
+  template <typename R, int N, int E, int THREADS>
+  __device__ __forceinline__ void after_fwd(const cplx<R> (&)[5][E], const LPassArgs<R>&, int, int, bool, int, int,
+                                            int, size_t) const {}
+  template <typename R, int N, int E>
+  __device__ __forceinline__ void after_mix(const cplx<R> (&)[5][E], const LPassArgs<R>&, bool, size_t) const {}
+};
+
+template <typename R, int N, int E, int G, bool CG = false, bool TMA = false, class Hook = NoHook>
 __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int plane, int member,
                                               unsigned char* smem_raw,
-                                              const CUtensorMap* tmap = nullptr) {
+                                              const CUtensorMap* tmap = nullptr, const Hook& hook = Hook()) {
   typedef cplx<R> C;
   typedef LCfg<R, N, E, G> Cfg;
   constexpr int T = Cfg::T;
@@ -1098,6 +1123,10 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
   C* b0 = xb + col * Cfg::LP;
   const int bstride = TILE * Cfg::LP;
   if (a.mode & LP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB>(v, i, tw, b0, bstride);
+  // thread i of column xcol holds line elements i + T e; the tile's
+  // element offset of (c, e) is base - field + c ntot + e step
+  hook.template after_fwd<R, N, E, Cfg::THREADS>(v, a, i, xcol, valid, plane, member, bx,
+                                                  (size_t)(base - a.field));
   if (a.mode & LP_MIX) {
     const int pm = valid ? xcol : 0;   // idle threads of a ragged tile read mode 0
     if (stab) {
@@ -1134,6 +1163,7 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
       }
     }
   }
+  hook.template after_mix<R, N, E>(v, a, valid, (size_t)(base - a.field));
   if (a.mode & LP_INV) fft_lines<R, N, E, +1, 5, Cfg::NB>(v, i, tw, b0, bstride);
   if constexpr (TMA) {
     // the five components out through the two exchange buffers: each is
