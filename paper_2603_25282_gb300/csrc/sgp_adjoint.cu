@@ -81,18 +81,18 @@ __global__ void __launch_bounds__(kXAdjThreads, 2) k_xadj(XAdjArgs<R> a) {
     q.c0p = (R)(P.c0 + P.c2 / 5.0);
     q.c1 = (R)P.c1;
     q.c2 = (R)P.c2;
-    q.dgg = 2.0 * (P.gx2h - P.gy2h);
-    q.tsub = s_rot[2];
-    const double co = s_rot[0], si = s_rot[1];
+    q.tdgg = (R)(s_rot[2] * 2.0 * (P.gx2h - P.gy2h));
+    const R co = (R)s_rot[0], si = (R)s_rot[1];
+    const R gx2h = (R)P.gx2h, gy2h = (R)P.gy2h, gz2h = (R)P.gz2h;
 #pragma unroll 1
     for (int p = tid; p < ROWS * N; p += kXAdjThreads) {
       const int r = p / N, j = p - r * N;
       const int rw = blockIdx.x * ROWS + r;
       if (rw >= a.rows) break;          // p only grows
       const int iy = rw % a.ny, iz = rw / a.ny;
-      const double x = a.x0 + j * a.hx, y = a.y0 + iy * a.hy, z = a.z0 + iz * a.hz;
-      const double xr = co * x + si * y, yr = co * y - si * x;
-      const R V = (R)(P.gx2h * xr * xr + P.gy2h * yr * yr + P.gz2h * z * z);
+      const R x = a.x0 + (R)j * a.hx, y = a.y0 + (R)iy * a.hy, z = a.z0 + (R)iz * a.hz;
+      const R xr = co * x + si * y, yr = co * y - si * x;
+      const R V = gx2h * xr * xr + gy2h * yr * yr + gz2h * z * z;
       const C* pr = a.phi + mo + (size_t)rw * N + j;
       C* sp = xb + r * Cfg::LP + j;
       C psi[5], gp[5];
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kXAdjThreads, 2) k_xadj(XAdjArgs<R> a) {
         psi[c] = pr[(size_t)c * a.ntot];
         gp[c] = sp[c * bstride];
       }
-      nl_adjoint_point<R>(psi, gp, V, xr, yr, q, acc);
+      nl_adjoint_point<R>(psi, gp, V, xr * yr, q, acc);
 #pragma unroll
       for (int c = 0; c < 5; ++c) sp[c * bstride] = gp[c];
     }
@@ -190,11 +190,14 @@ cudaError_t linepass_adj_n(const LPassArgs<Real>& a, const AdjHook<Real>& h, int
   constexpr int E = elems_per_thread<Real, N>();
   constexpr int G = kAdjLineGeom;
   typedef LCfg<Real, N, E, G> Cfg;
+  // the hook's staging sits behind the largest mode-table region
+  constexpr size_t HB = AdjHook<Real>::smem_bytes<Real, N, Cfg::TILE>();
+  static_assert(Cfg::SMEM + Cfg::TAB + HB <= 227 * 1024, "line pass of a gradient: shared memory");
   static int done = -1;
-  const cudaError_t e = opt_in(k_linepass_adj<Real, N, E, G>, Cfg::SMEM + Cfg::TAB, &done);
+  const cudaError_t e = opt_in(k_linepass_adj<Real, N, E, G>, Cfg::SMEM + Cfg::TAB + HB, &done);
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + Cfg::TILE - 1) / Cfg::TILE, planes, members);
-  const size_t smem = Cfg::SMEM + line_table_bytes<Cfg>(a.mode, a.axis);
+  const size_t smem = Cfg::SMEM + Cfg::TAB + (h.spec ? HB : 0);
   k_linepass_adj<Real, N, E, G><<<grid, Cfg::THREADS, smem, s>>>(a, h);
   return cudaGetLastError();
 }

@@ -98,24 +98,26 @@ __device__ __forceinline__ void apply_spin(const cplx<R> (&v)[5], const SpinRot<
   }
 }
 
-// Member constants of the nonlinear adjoint: the substep size d, c0 + c2/5,
-// c1, c2 in the field precision; 2 (gx^2 - gy^2)/2 and the substep time in FP64.
+// Member constants of the nonlinear adjoint in the field precision: the
+// substep size d, c0 + c2/5, c1, c2, and t (gx^2 - gy^2) at the substep's
+// time t (the factor of the Omega term).
 template <typename R>
 struct NLAdjPrm {
-  R d, c0p, c1, c2;
-  double dgg, tsub;
+  R d, c0p, c1, c2, tdgg;
 };
 
 // Nonlinear flow at one point: g <- -i DN_{-d}(Phi_out)[i g] with psi =
 // Phi_out there, and the parameter terms d Re<g, X_p(Phi_out)> added to acc
-// (slots NLA_*).  N = (phase) o (spin rotation) o (singlet rotation) as in
+// (slots NLA_*; each term formed in the field precision, the sums kept in
+// FP64).  N = (phase) o (spin rotation) o (singlet rotation) as in
 // Eq. (solution2); the tangent is carried through the same three factors of
 // N_{-d} at Phi_out.  rho, F and |A00| are the same at every stage
 // (conserved), so their tangents are formed once from the input tangent.
-// V: the trap at the mapped point; xr, yr: the mapped coordinates (FP64).
+// V: the trap at the mapped point; xy = xr yr, the mapped coordinates'
+// product.
 template <typename R>
-__device__ __forceinline__ void nl_adjoint_point(const cplx<R> (&psi)[5], cplx<R> (&g)[5], R V, double xr,
-                                                 double yr, const NLAdjPrm<R>& q, double (&acc)[NLA_NT]) {
+__device__ __forceinline__ void nl_adjoint_point(const cplx<R> (&psi)[5], cplx<R> (&g)[5], R V, R xy,
+                                                 const NLAdjPrm<R>& q, double (&acc)[NLA_NT]) {
   typedef cplx<R> C;
   const R r6 = (R)2.44948974278317809820;
   const R rs5 = (R)0.44721359549995793928;
@@ -139,11 +141,10 @@ __device__ __forceinline__ void nl_adjoint_point(const cplx<R> (&psi)[5], cplx<R
     spin_dot5<R>(Fp.x, Fp.y, Fz, psi, Fpsi);
     const C ip = inner5(g, psi);
     const C ia = inner5(g, ac);
-    const double ipi = (double)ip.y;
-    acc[NLA_C0] += (double)d * (double)rho * ipi;
-    acc[NLA_C1] += (double)d * (double)inner5(g, Fpsi).y;
-    acc[NLA_C2] += (double)d * (double)cmul(A00, ia).y * (double)rs5;
-    acc[NLA_OMEGA] += (double)d * q.tsub * q.dgg * xr * yr * ipi;
+    acc[NLA_C0] += (double)(d * rho * ip.y);
+    acc[NLA_C1] += (double)(d * inner5(g, Fpsi).y);
+    acc[NLA_C2] += (double)(d * cmul(A00, ia).y * rs5);
+    acc[NLA_OMEGA] += (double)(d * q.tdgg * xy * ip.y);
   }
   // tangent v = i g at Phi_out
   C v[5];
@@ -230,12 +231,12 @@ __device__ __forceinline__ void nl_adjoint_point(const cplx<R> (&psi)[5], cplx<R
 
 // Linear flow at one mode (signed indices ps, qs of the x and y wavenumbers
 // nu = (pxl ps, pyl qs), pxl = pi/Lx, pyl = pi/Ly): the derivatives in
-// Omega and gamma, -Re<g^, i (w.f) S^> times scale, added to acc[LPA_*].
+// Omega and gamma, -Re<g^, i (w.f) S^>, added to acc[LPA_*] (each formed in
+// the field precision, the sums kept in FP64; the caller scales the sums).
 // gv, sv: the mode of the transforms of g and of Phi_out.
 template <typename R>
 __device__ __forceinline__ void lin_param_mode(const cplx<R> (&gv)[5], const cplx<R> (&sv)[5], int ps, int qs,
-                                               R gamma, R omega, R dR, R pxl, R pyl, double scale,
-                                               double (&acc)[LPA_NT]) {
+                                               R gamma, R omega, R dR, R pxl, R pyl, double (&acc)[LPA_NT]) {
   typedef cplx<R> C;
   const R r6R = (R)2.44948974278317809820;
   // P+ = <g, f+ s>, P- = <g, f- s>, Pz = <g, fz s> in the field precision
@@ -246,10 +247,9 @@ __device__ __forceinline__ void lin_param_mode(const cplx<R> (&gv)[5], const cpl
   const C Pz = cadd(cscale(csub(cconjmul(gv[0], sv[0]), cconjmul(gv[4], sv[4])), (R)2),
                     csub(cconjmul(gv[1], sv[1]), cconjmul(gv[3], sv[3])));
   // Im<g, (w.f) s> = wx Im(P+ + P-)/2 - wy Re(P+ - P-)/2 + wz Im Pz
-  const double kx = 0.5 * ((double)Pp.y + (double)Pm.y);
-  const double ky = -0.5 * ((double)Pp.x - (double)Pm.x);
-  const double kz = (double)Pz.y;
-  // w in the field precision (its rounding enters the sum once)
+  const R kx = (R)0.5 * (Pp.y + Pm.y);
+  const R ky = (R)-0.5 * (Pp.x - Pm.x);
+  const R kz = Pz.y;
   const R nxR = pxl * (R)ps, nyR = pyl * (R)qs;
   const R ax = dR * (-gamma * nyR), ay = dR * (gamma * nxR), az = dR * (-omega);
   const R th2 = ax * ax + ay * ay + az * az;
@@ -274,7 +274,7 @@ __device__ __forceinline__ void lin_param_mode(const cplx<R> (&gv)[5], const cpl
     const R wx = px + sk * (dx - px) - ck * (hy * dz - hz * dy);
     const R wy = py + sk * (dy - py) - ck * (hz * dx - hx * dz);
     const R wz = pz + sk * (dz - pz) - ck * (hx * dy - hy * dx);
-    acc[p] -= scale * ((double)wx * kx + (double)wy * ky + (double)wz * kz);
+    acc[p] -= (double)(wx * kx + wy * ky + wz * kz);
   }
 }
 
@@ -293,7 +293,7 @@ struct XAdjArgs {
   long long ntot;
   int rows, ny;
   int mode;                 // XP_INV | XP_FWD
-  double x0, hx, y0, hy, z0, hz;
+  R x0, hx, y0, hy, z0, hz;  // coordinates x_j = x0 + j hx as in the x-pass
   double delta;             // forward substep size
   const double* t_base;     // the substep's time is *t_base + t_off
   double t_off;
@@ -318,35 +318,62 @@ struct AdjHook {
   double* partials;
   int prows, prow0, tiles;
   double Lx, Ly, delta, scale;
+  // bytes of shared memory the hook stages: the tile of spec
+  template <typename RR, int N, int TILE>
+  static constexpr size_t smem_bytes() { return (size_t)5 * N * TILE * sizeof(cplx<RR>); }
+  // the tile of spec ([component][line element][column]) to shared memory
+  // by asynchronous copies, issued before the field loads
+  template <typename RR, int N, int E, int TILE, int THREADS>
+  __device__ __forceinline__ void prefetch(unsigned char* hsm, const LPassArgs<RR>& a, int bx, int plane,
+                                           int member) const {
+    typedef cplx<RR> C;
+    if (!spec) return;
+    const C* src = spec + (size_t)member * 5 * a.ntot + (size_t)plane * a.plane_stride + (size_t)bx * TILE;
+    C* dst = reinterpret_cast<C*>(hsm);
+    for (int k = threadIdx.x; k < 5 * N * TILE; k += THREADS) {
+      const int cl = k % TILE, ln = (k / TILE) % N, c = k / (TILE * N);
+      if (bx * TILE + cl >= a.nx) continue;
+      const C* from = src + (size_t)c * a.ntot + (size_t)ln * a.line_stride + cl;
+      if constexpr (sizeof(C) == 16) cp_async16(dst + k, from);
+      else cp_async8(dst + k, from);
+    }
+    cp_async_commit();
+  }
   template <typename RR, int N, int E, int THREADS>
   __device__ __forceinline__ void after_fwd(const cplx<RR> (&v)[5][E], const LPassArgs<RR>& a, int i, int xcol,
-                                            bool valid, int plane, int member, int bx, size_t off) const {
+                                            bool valid, int plane, int member, int bx, size_t,
+                                            const unsigned char* hsm) const {
     typedef cplx<RR> C;
     constexpr int T = N / E;
+    constexpr int TILE = THREADS / T;
     constexpr double kPi = 3.14159265358979323846;
     if (!spec) return;                 // the same for every thread of the launch
     __shared__ double red[(THREADS + 31) / 32 * LPA_NT];
+    cp_async_wait();
+    __syncthreads();                   // the tile of spec is in shared memory
     const MemberPrm& P = mp[member];
     double acc[LPA_NT] = {0.0, 0.0};
     if (valid) {
       const RR pxl = (RR)(kPi / Lx), pyl = (RR)(kPi / Ly);
       const RR gam = (RR)P.gamma, om = (RR)P.omega, dR = (RR)delta;
       const int ps = xcol < a.NX / 2 ? xcol : xcol - a.NX;
-      const C* sp = spec + off;        // off includes the member's offset
-      const size_t step = (size_t)T * a.line_stride;
+      const C* sp = reinterpret_cast<const C*>(hsm) + (xcol - bx * TILE);
 #pragma unroll 1
       for (int e = 0; e < E; ++e) {
         // the mode's y index: the line element (y lines) or the plane (z lines)
-        const int q = a.axis == 1 ? i + T * e : plane;
+        const int ln = i + T * e;
+        const int q = a.axis == 1 ? ln : plane;
         const int qs = q < a.NY / 2 ? q : q - a.NY;
         C gv[5], sv[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           gv[c] = v[c][e];
-          sv[c] = sp[(size_t)c * a.ntot + e * step];
+          sv[c] = sp[((size_t)c * N + ln) * TILE];
         }
-        lin_param_mode<RR>(gv, sv, ps, qs, gam, om, dR, pxl, pyl, scale, acc);
+        lin_param_mode<RR>(gv, sv, ps, qs, gam, om, dR, pxl, pyl, acc);
       }
+      acc[0] *= scale;
+      acc[1] *= scale;
     }
     double out[LPA_NT];
     block_sums<LPA_NT>(acc, out, red);

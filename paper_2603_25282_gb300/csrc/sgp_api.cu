@@ -1138,12 +1138,12 @@ sgp_status adjoint_nonlinear(sgp_ctx* c, const void* phi, double delta, double t
   a.rows = c->n[1] * c->n[2];
   a.ny = c->n[1];
   a.mode = mode;
-  a.x0 = -c->L[0];
-  a.hx = c->h[0];
-  a.y0 = -c->L[1];
-  a.hy = c->h[1];
-  a.z0 = c->dim == 3 ? -c->L[2] : 0.0;
-  a.hz = c->dim == 3 ? c->h[2] : 0.0;
+  a.x0 = (R)-c->L[0];
+  a.hx = (R)c->h[0];
+  a.y0 = (R)-c->L[1];
+  a.hy = (R)c->h[1];
+  a.z0 = c->dim == 3 ? (R)-c->L[2] : (R)0;
+  a.hz = c->dim == 3 ? (R)c->h[2] : (R)0;
   a.delta = delta;
   a.t_base = c->t_dev;
   a.t_off = t_off;

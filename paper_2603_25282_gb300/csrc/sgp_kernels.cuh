@@ -649,6 +649,11 @@ __device__ __forceinline__ void cp_async16(void* dst_shared, const void* src_glo
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src_global) : "memory");
 }
+// 8-byte asynchronous copy global -> shared (through L1)
+__device__ __forceinline__ void cp_async8(void* dst_shared, const void* src_global) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src_global) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -996,10 +1001,14 @@ k_xyplane(XPassArgs<R> a, const TwE<R>* __restrict__ twy_g, int* err) {
 // flow after the forward transform (the tile then holds the full transform
 // of g), and the recomputation keeps a copy of the tile after the mix.  The
 // forward passes take NoHook.
+// A hook may also stage data of its own in shared memory behind the mode
+// table's region (hsm), with copies it starts before the field loads.
 struct NoHook {
+  template <typename R, int N, int E, int TILE, int THREADS>
+  __device__ __forceinline__ void prefetch(unsigned char*, const LPassArgs<R>&, int, int, int) const {}
   template <typename R, int N, int E, int THREADS>
   __device__ __forceinline__ void after_fwd(const cplx<R> (&)[5][E], const LPassArgs<R>&, int, int, bool, int, int,
-                                            int, size_t) const {}
+                                            int, size_t, const unsigned char*) const {}
   template <typename R, int N, int E>
   __device__ __forceinline__ void after_mix(const cplx<R> (&)[5][E], const LPassArgs<R>&, bool, size_t) const {}
 };
@@ -1070,6 +1079,8 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
     }
     cp_async_commit();
   }
+  unsigned char* hsm = reinterpret_cast<unsigned char*>(smt) + Cfg::TAB;
+  hook.template prefetch<R, N, E, TILE, Cfg::THREADS>(hsm, a, bx, plane, member);
   C* base = a.field + (size_t)member * 5 * a.ntot + (size_t)plane * a.plane_stride +
             (valid ? xcol : 0) + (size_t)i * a.line_stride;
   const size_t step = (size_t)T * a.line_stride;
@@ -1126,7 +1137,7 @@ __device__ __forceinline__ void linepass_body(const LPassArgs<R>& a, int bx, int
   // thread i of column xcol holds line elements i + T e; the tile's
   // element offset of (c, e) is base - field + c ntot + e step
   hook.template after_fwd<R, N, E, Cfg::THREADS>(v, a, i, xcol, valid, plane, member, bx,
-                                                  (size_t)(base - a.field));
+                                                  (size_t)(base - a.field), hsm);
   if (a.mode & LP_MIX) {
     const int pm = valid ? xcol : 0;   // idle threads of a ragged tile read mode 0
     if (stab) {
