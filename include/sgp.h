@@ -332,12 +332,12 @@ sgp_status sgp_observables(sgp_ctx* ctx, sgp_obs* out);
  * `interval` steps (interval = 0: ceil(sqrt(nsteps))) in device memory
  * owned by the context, for sgp_backward.  The record stays valid until the
  * next sgp_set_state, sgp_set_params(_batch), sgp_step, sgp_substep or
- * sgp_record.  Memory: ceil(nsteps/interval) states for the checkpoints and
- * interval*(substeps per step) + 1 states (3 for TS2, 7 for TS4) for one
- * recomputed segment in sgp_backward; when it can be had, two such buffers
- * with room for interval*(linear substeps per step) more states each (the
- * next segment is then recomputed on a second stream during the sweep
- * through the current one).  Errors: SGP_EINVAL for nsteps <= 0,
+ * sgp_record.  Memory: ceil(nsteps/interval) states for the checkpoints and,
+ * for one recomputed segment in sgp_backward, interval*(substeps per step)
+ * + 1 states (3 for TS2, 7 for TS4) plus interval*(linear substeps per
+ * step) states for the linear substeps' outputs in transform space; when it
+ * can be had, a second such buffer (the next segment is then recomputed on
+ * a second stream during the sweep through the current one).  Errors: SGP_EINVAL for nsteps <= 0,
  * interval < 0 or dt/scheme as in sgp_step; SGP_ESTATE before
  * sgp_set_state; SGP_ENOMEM/SGP_ECUDA on allocation or launch failure. */
 sgp_status sgp_record(sgp_ctx* ctx, long long nsteps, double dt, int scheme,
