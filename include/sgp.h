@@ -262,8 +262,8 @@ sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
 
 /* ---------------------------------------------------------------------
  * Kernel variants (FFT tile and radix schedules) and the autotuner.
- * Every pass kernel exists in up to five variants per line length N, and
- * 3D grids have a sixth, plane-level variant of the x-pass:
+ * Every pass kernel exists in up to six variants per line length N, and
+ * 3D grids have a plane-level variant of the x-pass:
  *   0  default: x-pass CTAs of about 256 threads (rows side by side), line
  *      pass up to 512 threads with TILE >= 4 (FP32) / 2 (FP64) columns;
  *   1  CTAs of about half the threads (line pass TILE down to 1);
@@ -280,12 +280,16 @@ sgp_status sgp_set_graphs(sgp_ctx* ctx, int enable);
  *      y transforms (the plane moves between the CTAs through distributed
  *      shared memory), so a step runs no y-line passes: two passes per
  *      linear/nonlinear pair instead of four.  Other x-passes (gradients,
- *      observables) are those of variant 1.
+ *      observables) are those of variant 1;
+ *   6  x-pass: CTAs of variant 2's rows with the nonlinear flow shared by
+ *      256 threads (for small grids, whose CTAs are few, each thread takes
+ *      fewer points through the flow); line pass: the same as variant 2.
  * A plan is one variant per axis (x-pass, y lines, z lines).  Variants
  * compute the same transforms with different rounding (variant 3 has a
  * different radix plan), so results agree to rounding, not bit for bit;
  * variant 4 agrees with variant 1 bit for bit, and variant 5 with variant
- * 1 when the y axis runs variant 0, 1, 2 or 4.
+ * 1 when the y axis runs variant 0, 1, 2 or 4; x-pass variant 6 agrees
+ * with variant 2 to rounding.
  * ------------------------------------------------------------------- */
 /* 1 if variant v exists for line length n at precision prec, else 0
  * (also for arguments out of range, and for variant 5, which depends on
@@ -305,9 +309,10 @@ sgp_status sgp_get_plan(const sgp_ctx* ctx, int* variants);
  * variant must be at least 1.5% faster to replace a lower one).  The state
  * and the time are not changed.  Results are cached per process by
  * (device, precision, grid, batch); a cached plan is reused unless flags
- * has SGP_TUNE_FORCE or ms_out is given.  ms_out (may be NULL): 3 x 6
+ * has SGP_TUNE_FORCE or ms_out is given.  ms_out (may be NULL): 3 x 7
  * doubles, ms per step of [axis][variant], -1 where the variant or axis
- * does not exist and for variant 4 of the x-pass (which is variant 1).
+ * does not exist, for variant 4 of the x-pass (which is variant 1) and for
+ * variant 6 of the line passes (which is variant 2).
  * Synchronises.  Allocates one field-sized scratch buffer
  * for the duration of the call.  Errors: SGP_EINVAL for a NULL ctx or reps
  * outside [1, 1000]; SGP_ENOMEM / SGP_ECUDA for the scratch or a launch. */

@@ -1748,7 +1748,7 @@ std::string tune_key(const sgp_ctx* c) {
 // warm-up step: the data stay a physical state, so the nonlinear flow takes
 // its usual branches, and the pass interplay of a real step is included.  A
 // variant replaces an earlier (lower-numbered) one only when it is at least
-// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][6]:
+// 1.5% faster, so near-ties resolve the same way run to run.  ms_out[3][7]:
 // ms per step with that variant (-1 where a variant does not exist or the
 // axis is absent).
 template <typename R>
@@ -1772,6 +1772,7 @@ sgp_status autotune_impl(sgp_ctx* c, int reps, double* ms_out) {
     for (int v = 0; v < kVariants && st == SGP_OK; ++v) {
       if (!axis_variant_ok(c, a, v)) continue;
       if (a == 0 && v == 4) continue;     // the x-pass of variant 4 is variant 1
+      if (a != 0 && v == 6) continue;     // the line pass of variant 6 is variant 2
       if (v == 4 && !tensor_map_encoder()) continue;
       st = use_variant(c, a, v);
       if (st != SGP_OK) break;

@@ -147,6 +147,53 @@ cudaError_t launch_xyplane(int N, const XPassArgs<Real>& a, const TwE<Real>* twy
 }
 #endif
 
+#if SGP_VAR == 2
+// x-pass variant 6 (k_xpass_wide): geometry 2, compiled with variant 2
+template <int N>
+static cudaError_t xpass_wide_prepare_n() {
+  constexpr int E = elems_per_thread<Real, N>();
+  static int done = -1;
+  return prepare(k_xpass_wide<Real, N, E>, XCfg<Real, N, E, 2>::SMEM, &done);
+}
+
+template <>
+cudaError_t prepare_xpass_wide<Real>(int N) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return xpass_wide_prepare_n<NN>();
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+static cudaError_t xpass_wide_n(const XPassArgs<Real>& a, int members, cudaStream_t s) {
+  constexpr int E = elems_per_thread<Real, N>();
+  typedef XCfg<Real, N, E, 2> Cfg;
+  cudaError_t e = xpass_wide_prepare_n<N>();
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.rows + Cfg::ROWS - 1) / Cfg::ROWS, members);
+  k_xpass_wide<Real, N, E><<<grid, kXWideThreads, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_xpass_wide<Real>(int N, const XPassArgs<Real>& a, int members, cudaStream_t s) {
+  switch (N) {
+#define SGP_CASE(NN) \
+  case NN:           \
+    return xpass_wide_n<NN>(a, members, s);
+    SGP_FOR_EACH_N(SGP_CASE)
+#undef SGP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+#endif
+
 #if SGP_VAR == 0
 template <int N>
 static cudaError_t obs_x_n(const ObsXArgs<Real>& a, int members, cudaStream_t s) {

@@ -579,6 +579,113 @@ k_xpass(XPassArgs<R> a) {
   xpass_body<R, N, E, G>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// x-pass variant 6 (small grids): the rows of x-pass geometry 2 (about 64
+// threads side by side) transformed by their FT threads, and the nonlinear
+// flow at the rows' points shared by all kXWideThreads threads of the CTA.
+// A small grid fills few SMs, and a thread of the other variants takes its
+// E points through the flow one after the other; here each takes
+// ROWS * N / kXWideThreads.  The transforms synchronise with a named
+// barrier of the FT threads; the arithmetic per line and per point is that
+// of the other variants with the same elements per thread.
+constexpr int kXWideThreads = 256;
+
+template <typename R, int N, int E>
+__global__ void __launch_bounds__(kXWideThreads, 2) k_xpass_wide(XPassArgs<R> a) {
+  typedef cplx<R> C;
+  typedef XCfg<R, N, E, 2> Cfg;
+  constexpr int T = Cfg::T, FT = Cfg::THREADS, ROWS = Cfg::ROWS;
+  static_assert(kXWideThreads % FT == 0 && FT % 32 == 0, "x-pass variant 6 geometry");
+  constexpr int GT = FT == kXWideThreads ? 0 : FT;      // the transforms' barrier
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TwE<R>* tw = reinterpret_cast<TwE<R>*>(smem_raw);
+  C* xb = reinterpret_cast<C*>(tw + N);
+  __shared__ R s_prm[8];
+  __shared__ R s_yz[ROWS][2];
+  const int member = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int g = tid / T;
+  const int i = tid - g * T;
+  for (int k = tid; k < N; k += kXWideThreads) tw[k] = a.tw[k];
+  if ((a.mode & XP_NL) && tid == 0) {
+    const MemberPrm& P = a.mp[member];
+    const double t = *a.t_base + a.t_off;
+    double sn, cs;
+    sincos(P.omega * t, &sn, &cs);
+    s_prm[0] = (R)cs;
+    s_prm[1] = (R)sn;
+    s_prm[2] = (R)(P.c0 + P.c2 / 5.0);
+    s_prm[3] = (R)P.c1;
+    s_prm[4] = (R)P.c2;
+    s_prm[5] = (R)P.gx2h;
+    s_prm[6] = (R)P.gy2h;
+    s_prm[7] = (R)P.gz2h;
+  }
+  if ((a.mode & XP_NL) && tid < ROWS) {
+    const int rr = blockIdx.x * ROWS + tid;
+    s_yz[tid][0] = a.y0 + (R)(rr % a.ny) * a.hy;
+    s_yz[tid][1] = a.z0 + (R)(rr / a.ny) * a.hz;
+  }
+  const int bstride = ROWS * Cfg::LP;
+  const int row = blockIdx.x * ROWS + g;
+  const bool valid = tid < FT && row < a.rows;
+  C* base = a.field + (size_t)member * 5 * a.ntot + (size_t)(valid ? row : 0) * N + i;
+  C* b0 = xb + g * Cfg::LP;
+  C v[5][E];
+  if (tid < FT) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[c][e] = valid ? base[(size_t)c * a.ntot + T * e] : mkc((R)0, (R)0);
+  }
+  __syncthreads();                    // twiddles, s_prm, s_yz
+  if (tid < FT && (a.mode & XP_INV)) fft_lines<R, N, E, +1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, 1);
+  if (a.mode & XP_NL) {
+    if (tid < FT) {
+      group_sync<GT>(1);              // the exchanges' reads of the buffers are done
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+#pragma unroll
+        for (int e = 0; e < E; ++e) b0[c * bstride + i + T * e] = v[c][e];
+    }
+    __syncthreads();                  // the rows are staged
+    const R co = s_prm[0], si = s_prm[1];
+    const R c0p = s_prm[2], c1 = s_prm[3], c2 = s_prm[4];
+    const R gx2h = s_prm[5], gy2h = s_prm[6], gz2h = s_prm[7];
+#pragma unroll 1
+    for (int p = tid; p < ROWS * N; p += kXWideThreads) {
+      const int r = p / N, j = p - r * N;
+      if (blockIdx.x * ROWS + r >= a.rows) break;     // p only grows
+      const R y = s_yz[r][0];
+      const R zz = gz2h * s_yz[r][1] * s_yz[r][1];
+      const R x = a.x0 + (R)j * a.hx;
+      const R xr = co * x + si * y;
+      const R yr = co * y - si * x;
+      const R V = gx2h * xr * xr + gy2h * yr * yr + zz;
+      C* pp = xb + r * Cfg::LP + j;
+      C q[5] = {pp[0], pp[bstride], pp[2 * bstride], pp[3 * bstride], pp[4 * bstride]};
+      nonlinear_point<R>(q, V, a.delta, c0p, c1, c2);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) pp[c * bstride] = q[c];
+    }
+    __syncthreads();                  // every point is done
+    if (tid < FT) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[c][e] = b0[c * bstride + i + T * e];
+    }
+  }
+  if (tid < FT) {
+    if (a.mode & XP_FWD) fft_lines<R, N, E, -1, 5, Cfg::NB, GT>(v, i, tw, b0, bstride, 1);
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+#pragma unroll
+        for (int e = 0; e < E; ++e) base[(size_t)c * a.ntot + T * e] = v[c][e];
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------
 // line-pass kernel (strided lines, tile of TILE consecutive x positions)
 // ----------------------------------------------------------------------------

@@ -48,7 +48,10 @@ inline bool supported_n(int n) {
 //      x-passes become xy-plane passes (k_xyplane: one thread-block cluster
 //      per z plane, the y transforms done there), so a step drops its
 //      y-line passes; x-passes outside the steps are those of variant 1
-constexpr int kVariants = 6;
+//   6  x-pass: the rows of geometry 2 with the nonlinear flow shared by the
+//      256 threads of the CTA (k_xpass_wide; for small grids, whose CTAs
+//      are few); line pass: the same as variant 2
+constexpr int kVariants = 7;
 
 template <typename R, int N, int V>
 constexpr int variant_elems() {
@@ -57,7 +60,7 @@ constexpr int variant_elems() {
 // geometry of variant V for the x-pass (PART 0) and the line pass (PART 1)
 template <int N, int V, int PART>
 constexpr int variant_geom() {
-  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : (V == 4 || V == 5) ? 1 : V;
+  return V == 3 ? (N % 3 == 0 ? 1 + PART : 0) : (V == 4 || V == 5) ? 1 : V == 6 ? 2 : V;
 }
 
 // Does variant V exist for line length N (prec_bytes 4 or 8)?
@@ -100,9 +103,16 @@ PassGeom linepass_geom_tma(int N);
 cudaError_t launch_xyplane(int N, const XPassArgs<float>& a, const TwE<float>* twy, int* err, int planes,
                            int members, cudaStream_t s);
 cudaError_t prepare_xyplane(int N);
+// Variant 6 of the x-pass (k_xpass_wide).
+template <typename R>
+cudaError_t launch_xpass_wide(int N, const XPassArgs<R>& a, int members, cudaStream_t s);
+template <typename R>
+cudaError_t prepare_xpass_wide(int N);
 
 // x-pass variants 4 and 5 are variant 1 (variant 5's plane pass has its own
-// entry point); the line pass has its own variant 4
+// entry point) and variant 6 has the geometry of variant 2 (its own kernel,
+// dispatched first); the line pass has its own variant 4 and takes variant
+// 2 for 6
 #define SGP_VARIANT_SWITCH_X(V, CALL, FAIL)                  \
   switch (V) {                                               \
     case 0: return CALL(0);                                  \
@@ -115,6 +125,7 @@ cudaError_t prepare_xyplane(int N);
     case 5:                                                  \
       if constexpr (sizeof(R) == 4) return CALL(1);          \
       return FAIL;                                           \
+    case 6: return CALL(2);                                  \
     default: return FAIL;                                    \
   }
 #define SGP_VARIANT_SWITCH(V, CALL, FAIL)                    \
@@ -125,6 +136,7 @@ cudaError_t prepare_xyplane(int N);
     case 3:                                                  \
       if constexpr (sizeof(R) == 4) return CALL(3);          \
       return FAIL;                                           \
+    case 6: return CALL(2);                                  \
     default: return FAIL;                                    \
   }
 
@@ -146,6 +158,10 @@ inline PassGeom linepass_geom(int N, int V = 0) {
 // current device (done before any stream capture).
 template <typename R>
 inline cudaError_t prepare_xpass(int N, int V = 0) {
+  if (V == 6) {
+    const cudaError_t e = prepare_xpass_wide<R>(N);
+    if (e != cudaSuccess) return e;
+  }
 #define SGP_C(v) prepare_xpass_v<R, v>(N)
   SGP_VARIANT_SWITCH_X(V, SGP_C, cudaErrorInvalidValue)
 #undef SGP_C
@@ -160,6 +176,7 @@ inline cudaError_t prepare_linepass(int N, int V = 0) {
 }
 template <typename R>
 inline cudaError_t launch_xpass(int N, int V, const XPassArgs<R>& a, int members, cudaStream_t s) {
+  if (V == 6) return launch_xpass_wide<R>(N, a, members, s);
 #define SGP_C(v) launch_xpass_v<R, v>(N, a, members, s)
   SGP_VARIANT_SWITCH_X(V, SGP_C, cudaErrorInvalidValue)
 #undef SGP_C

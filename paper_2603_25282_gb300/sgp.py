@@ -285,7 +285,7 @@ def step_host(ctx, src, t0, dst, nsteps, dt, scheme, chunks, dtype):
 
 
 SGP_TUNE_FORCE = 1
-N_VARIANTS = 6
+N_VARIANTS = 7
 
 
 def variant_exists(prec, n, variant):

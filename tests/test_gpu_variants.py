@@ -97,7 +97,8 @@ def test_autotune_keeps_state_and_matches_oracle(prec):
         assert sgp.variant_exists(prec, n[a], plan[a])
         assert ms[a][plan[a]] is not None and ms[a][plan[a]] > 0
         for v in range(sgp.N_VARIANTS):
-            timed = sgp.variant_exists(prec, n[a], v) and not (a == 0 and v == 4)
+            timed = (sgp.variant_exists(prec, n[a], v) and not (a == 0 and v == 4)
+                     and not (a != 0 and v == 6))
             assert (ms[a][v] is not None) == timed
     assert ms[2] == [None] * sgp.N_VARIANTS
     assert c.autotune(reps=5) == plan                     # cached
@@ -123,3 +124,29 @@ def test_ensemble_autotune_then_step():
         ref = O.Propagator(O.Grid(n, L), O.Params(**PRM)).run(psis[i], 0.0, 1e-3, 10, "ts2")[0]
         assert O.rel_l2(ens.get_member_state(i).astype(np.complex128), ref) < 1e-5
     ens.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n,L,steps", [((256, 256), 8.0, 130), ((96, 64), (7.0, 5.0), 12),
+                                       ((48, 32, 64), (6.0, 5.0, 7.0), 6)])
+def test_variant6_against_variant2(prec, n, L, steps):
+    """x-pass variant 6 (the rows of variant 2, the nonlinear flow shared by
+    all threads of the CTA) takes every line and point through the
+    arithmetic of variant 2 (130 steps replay a captured 64-step graph
+    twice).  FP64: the fields agree to rounding (the compiler may fuse the
+    other product of a sum of two products in another kernel).  FP32: the
+    flow's small-angle
+    form is chosen per warp, and a warp holds other points here, so the
+    fields differ at the level of FP32 rounding: variant 6 is as close to
+    the FP64 field as variant 2 is."""
+    psi = inputs.gaussian_random_phase(n, L, seed=8, amp=0.5)
+    rest = [0] * (len(n) - 1)
+    a = _run(n, L, prec, [2] + rest, psi, steps, 1e-3, "ts4" if len(n) == 2 else "ts2")
+    b = _run(n, L, prec, [6] + rest, psi, steps, 1e-3, "ts4" if len(n) == 2 else "ts2")
+    assert np.isfinite(a).all()
+    if prec == "f64":
+        assert O.rel_l2(b, a) < 1e-12
+    else:
+        ref = _run(n, L, "f64", [0] * len(n), psi, steps, 1e-3, "ts4" if len(n) == 2 else "ts2")
+        ea, eb = O.rel_l2(a, ref), O.rel_l2(b, ref)
+        assert eb < 1e-4 and eb <= 1.5 * ea + 1e-7, (ea, eb)
