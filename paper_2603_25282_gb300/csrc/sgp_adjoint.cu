@@ -27,11 +27,12 @@ typedef SGP_REAL Real;
 // all of them share the rows' points, staged in the exchange buffers;
 // Phi_out comes from global memory point by point.
 constexpr int kXAdjThreads = 256;
+constexpr int kXAdjGeom = 2;          // x-pass geometry of the rows
 
 template <typename R, int N, int E>
 __global__ void __launch_bounds__(kXAdjThreads, 2) k_xadj(XAdjArgs<R> a) {
   typedef cplx<R> C;
-  typedef XCfg<R, N, E, 2> Cfg;
+  typedef XCfg<R, N, E, kXAdjGeom> Cfg;
   constexpr int T = Cfg::T, FT = Cfg::THREADS, ROWS = Cfg::ROWS;
   static_assert(kXAdjThreads % FT == 0 && FT % 32 == 0, "adjoint x-pass geometry");
   constexpr int GT = FT == kXAdjThreads ? 0 : FT;       // the transforms' barrier
@@ -163,7 +164,7 @@ cudaError_t opt_in(K kern, size_t smem, int* done_dev) {
 template <int N>
 cudaError_t xadj_n(const XAdjArgs<Real>& a, int members, cudaStream_t s) {
   constexpr int E = elems_per_thread<Real, N>();
-  typedef XCfg<Real, N, E, 2> Cfg;
+  typedef XCfg<Real, N, E, kXAdjGeom> Cfg;
   static int done = -1;
   const cudaError_t e = opt_in(k_xadj<Real, N, E>, Cfg::SMEM, &done);
   if (e != cudaSuccess) return e;
@@ -249,7 +250,7 @@ int xadj_ctas<Real>(int N, int rows) {
   switch (N) {
 #define SGP_CASE(NN)                                               \
   case NN: {                                                       \
-    typedef XCfg<Real, NN, elems_per_thread<Real, NN>(), 2> Cfg;  \
+    typedef XCfg<Real, NN, elems_per_thread<Real, NN>(), kXAdjGeom> Cfg;  \
     return (rows + Cfg::ROWS - 1) / Cfg::ROWS;                     \
   }
     SGP_FOR_EACH_N(SGP_CASE)
