@@ -256,13 +256,13 @@ __device__ __forceinline__ void lin_param_mode(const cplx<R> (&gv)[5], const cpl
   const R das[2][3] = {{(R)0, (R)0, -dR}, {-dR * nyR, dR * nxR, (R)0}};
   R sk = (R)1, ck = (R)0, hx = (R)0, hy = (R)0, hz = (R)0;
   if (th2 > (R)0) {
-    const R th = sqrt(th2);
-    const R ith = (R)1 / th;
+    const R ith = rsqrt_r(th2);
+    const R th = th2 * ith;
     hx = ax * ith;
     hy = ay * ith;
     hz = az * ith;
     R sh, ch;
-    sincos_r((R)0.5 * th, &sh, &ch);
+    sincos_small((R)0.5 * th, &sh, &ch);   // series below 0.6 rad (FP32)
     sk = (R)2 * sh * ch * ith;             // sin th / th
     ck = (R)2 * sh * sh * ith;             // (1 - cos th) / th
   }
